@@ -1,0 +1,333 @@
+#!/usr/bin/env python
+"""Benchmark: converged steady-PSR solves/s on GB300, mixed-precision vs FP64 form.
+
+One step = one persistent-kernel solve of the whole batch (B = 4096 reactors per GPU of
+the K = 53 / I = 325 synthetic mechanism with 10 third-body and 15 Troe reactions,
+adiabatic, 1 atm, guess = inlet at 2000 K), inputs resident in HBM. The headline value
+is the mixed form (FP64 residual, FP32 Jacobian and LU); the FP64 form is timed on the
+same inputs. `e2e` times the host-pointer C entry (copies in, solve, copies out).
+Multi-GPU: one process per GPU, each solving its own seeded shard (no collective).
+
+`--impl reference` times the CPU oracle (plain numpy FP64) on a bounded sample of the
+same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+# the CPU oracle legs run single-threaded (reported as cores = 1)
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "k53_b4096"
+METRIC = "converged PSR solves/s, mixed vs FP64 form on one GB300 at ‖F‖∞≤1e-8; roofline %"
+UNIT = "solves/s"
+FP64_PEAK_TFLOPS = 1.25          # nominal GB300 FP64 (non-tensor) rate
+# FP64-pipe cost of one transcendental in flop slots (measured GB300 throughput of CUDA's
+# double exp / log relative to the FP64 FMA rate: 1.2 TFLOP/s / 29.6 G exp/s, / 16.3 G log/s)
+EXP_FLOPS, LOG_FLOPS, DIV_FLOPS = 40.0, 73.0, 16.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------- work model
+def fp64_work(mech_spec, nfev, iters, precision):
+    """FP64-pipe work (flops, transcendentals at their measured pipe cost) of the solver:
+    per residual evaluation W_F, per Newton iteration the Jacobian's FP64 part W_J and,
+    in the FP64 form, the LU (2n^3/3) and per residual one triangular solve pair (2n^2)."""
+    K, I = mech_spec.K, mech_spec.I
+    n = K + 1
+    n_tb = sum(r.kind == "tb" for r in mech_spec.reactions)
+    n_troe = sum(r.kind == "troe" for r in mech_spec.reactions)
+    n_eff = sum(len(r.eff) for r in mech_spec.reactions)
+    nnz = sum(len(set(r.reac) | set(r.prod)) for r in mech_spec.reactions)   # wdot gather entries
+    W_F = (K * 45 + I * (20 + 2 * EXP_FLOPS) + 2 * n_eff + 2 * nnz + K * 4
+           + n_troe * (4 * EXP_FLOPS + 2 * LOG_FLOPS + 30) + 2 * LOG_FLOPS + 4 * DIV_FLOPS)
+    W_J = I * 80 + 4 * nnz + 2 * K * K + 4 * K * K + (n_tb + n_troe) * 12 + n_troe * (60 + 4 * EXP_FLOPS + 2 * LOG_FLOPS)
+    W_LU = 2.0 * n ** 3 / 3.0 if precision == "fp64" else 0.0
+    W_S = 2.0 * n * n if precision == "fp64" else 0.0
+    nf, it = float(np.sum(nfev)), float(np.sum(iters))
+    return nf * (W_F + W_S) + it * (W_J + W_LU)
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (SM clock, throttle reasons) while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- oracle timing
+def oracle_time(name, indices):
+    from oracle import psr_oracle as O
+    from paper_2005_11468_gb300 import synth
+    spec = synth.workload_mechanism(name)
+    mech = O.Mechanism(synth.mechanism_text(spec))
+    batch = synth.workload_batch(name, spec)
+    t0 = time.perf_counter()
+    res = O.solve_batch(mech, batch, indices=list(indices))
+    dt = time.perf_counter() - t0
+    return int(np.sum(res["status"] == O.CONVERGED)), dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    K, W = args.steps, args.warmup
+    conv_total, t_total = 0, 0.0
+    for s in range(W + K):
+        c, dt = oracle_time(args.workload, [s])
+        if s >= W:
+            conv_total += c
+            t_total += dt
+    v = conv_total / t_total if t_total > 0 else 0.0
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": K, "warmup": W, "ms_per_step": 1e3 * t_total / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload} (one reactor of the batch per step)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"reactors 0..{W + K - 1} of {args.workload}, one per step, "
+                                       f"timed steps {W}..{W + K - 1}"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    from paper_2005_11468_gb300 import _build, psr, synth
+    if not os.path.exists(psr.LIB_PATH):
+        _build.build()
+    w = synth.WORKLOADS[args.workload]
+    spec = synth.workload_mechanism(args.workload)
+    mech = psr.Mechanism(synth.mechanism_text(spec))
+    batch = synth.make_batch(spec, w["B"], seed=synth.MECH_SEED_BASE + 10 * w["tag"] + 1 + 1000 * rank,
+                             tau_range=w.get("tau_range", (1e-4, 1e-2)))
+    t = {k: torch.tensor(getattr(batch, k), dtype=torch.float64, device=dev)
+         for k in ("Y_in", "T_in", "tau", "P", "Y0", "T0")}
+    B = batch.B
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    def timed(precision, steps, warmup, sampler=None):
+        opts = psr.Options(precision=precision)
+        out = None
+        for _ in range(warmup):
+            out = psr.batch_solve(mech, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"], opts=opts, out=out)
+        barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        conv = 0
+        nfev = iters = None
+        ctx = sampler if sampler is not None else _Null()
+        with ctx:
+            for s in range(steps):
+                flush.fill_(float(s))                     # evict the inputs from L2 between steps
+                ev[s][0].record(stream)
+                out = psr.batch_solve(mech, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"],
+                                      opts=opts, out=out)
+                ev[s][1].record(stream)
+            barrier()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        st = out["status"].cpu().numpy()
+        conv = int(np.sum(st == psr.PSR_CONVERGED))
+        nfev = out["nfev"].cpu().numpy()
+        iters = out["iters"].cpu().numpy()
+        total = sum(ms)
+        if pg is not None:
+            tt = torch.tensor([total], dtype=torch.float64, device=dev)
+            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+            total = tt.item()
+        return dict(ms=ms, total_ms=total, conv=conv, nfev=nfev, iters=iters)
+
+    K, W = args.steps, args.warmup
+    sampler = ClockSampler(local)
+    mixed = timed(psr.PSR_MIXED, K, W, sampler)
+    fp64 = timed(psr.PSR_FP64, max(1, min(K, 3)), 1)
+
+    # end to end through the host-pointer entry (inputs from pinned host memory)
+    host = {k: torch.tensor(getattr(batch, k), dtype=torch.float64).pin_memory()
+            for k in ("Y_in", "T_in", "tau", "P", "Y0", "T0")}
+    hout = dict(Y=torch.empty((B, spec.K), dtype=torch.float64).pin_memory(),
+                T=torch.empty(B, dtype=torch.float64).pin_memory(),
+                iters=torch.empty(B, dtype=torch.int32).pin_memory(),
+                ts_steps=torch.empty(B, dtype=torch.int32).pin_memory(),
+                status=torch.empty(B, dtype=torch.int32).pin_memory(),
+                fnorm=torch.empty(B, dtype=torch.float64).pin_memory(),
+                nfev=torch.empty(B, dtype=torch.int32).pin_memory())
+    eopts = psr.Options(precision=psr.PSR_MIXED)
+    psr.batch_solve_host(mech, host["Y_in"], host["T_in"], host["tau"], host["P"], host["Y0"], host["T0"],
+                         opts=eopts, out=hout)
+    barrier()
+    e_conv, e_t = 0, 0.0
+    for s in range(K):
+        flush.fill_(float(s))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        psr.batch_solve_host(mech, host["Y_in"], host["T_in"], host["tau"], host["P"], host["Y0"], host["T0"],
+                             opts=eopts, out=hout)
+        e_t += time.perf_counter() - t0
+        e_conv += int((hout["status"] == 0).sum())
+    if pg is not None:
+        tt = torch.tensor([e_t], dtype=torch.float64, device=dev)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        e_t = tt.item()
+    h2d = B * spec.K * 8 * 2 + B * 8 * 4
+    d2h = B * spec.K * 8 + B * 8 * 2 + B * 4 * 4
+
+    conv_all = mixed["conv"] * K
+    conv64 = fp64["conv"] * len(fp64["ms"])
+    if pg is not None:
+        c = torch.tensor([conv_all, conv64, e_conv], dtype=torch.float64, device=dev)
+        pg.all_reduce(c)
+        conv_all, conv64, e_conv = (float(x) for x in c.tolist())
+    value = conv_all / (mixed["total_ms"] / 1e3)
+    value64 = conv64 / (fp64["total_ms"] / 1e3)
+    e2e_value = e_conv / e_t
+
+    if rank != 0:
+        if pg is not None:
+            pg.destroy_process_group()
+        return
+    avg_ms = mixed["total_ms"] / K
+    work = fp64_work(spec, mixed["nfev"], mixed["iters"], "mixed")
+    achieved = work / (avg_ms / 1e3) / 1e12
+    work64 = fp64_work(spec, fp64["nfev"], fp64["iters"], "fp64")
+    achieved64 = work64 / (fp64["total_ms"] / len(fp64["ms"]) / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": avg_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 residual / f32 Jacobian+LU", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: K={spec.K} species, I={spec.I} reactions "
+                               f"(10 third-body, 15 Troe), B={B} reactors per GPU, adiabatic, 1 atm",
+                   "global_batch": B * world, "precision": "mixed", "parallelism": f"dp{world} (independent reactors)",
+                   "l2": "flushed (256 MB write) between timed steps"},
+        "fp64_form": {"value": value64, "unit": UNIT, "ms_per_step": fp64["total_ms"] / len(fp64["ms"]),
+                      "converged": fp64["conv"], "roofline_frac": achieved64 / FP64_PEAK_TFLOPS},
+        "mixed_vs_fp64": value / value64 if value64 > 0 else None,
+        "converged_fraction": mixed["conv"] / B,
+        "newton_iters_median": float(np.median(mixed["iters"])),
+        "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "nominal GB300 FP64 rate (recipe table); measured FMA loop 1.198",
+                     "work_model": "FP64 flops with exp=40, log=73, div=16 flop slots"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": K,
+        "clocks": sampler.summary(),
+    }
+    if not args.no_cpu_baseline:
+        idx = list(range(6))
+        c, dt = oracle_time(args.workload, idx)
+        line["cpu_baseline"] = {"value": c / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"reactors 0..5 of {args.workload} ({c} converged, {dt:.1f} s)"}
+    print(json.dumps(line))
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

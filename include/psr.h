@@ -1,0 +1,165 @@
+/* psr.h -- C ABI of libpsr, a batched steady-state perfectly-stirred-reactor (PSR)
+ * solver for NVIDIA GB300 (sm_103a).
+ *
+ * Method (Adhikari, Sayre & Chandy, "Towards using GPGPU units for accelerating the
+ * batched perfectly stirred reactor (PSR) calculations"): every reactor of a batch
+ * solves the steady form of the mass, species and energy balances of Sec. 2,
+ * Eqs. (1)-(3), with the net production rates of Sec. 3, Eqs. (4)-(9), by the hybrid
+ * Newton / pseudo-transient scheme of Sec. 3 (Newton iteration on the error vector
+ * with an LU-factored Jacobian; when Newton fails the estimate is conditioned by time
+ * integration and Newton is tried again). The batch is the paper's "n independent
+ * PSRs solved simultaneously" (Sec. 6).
+ *
+ * Conventions
+ *  - Every function returns an int status: PSR_OK (0) or a negative PSR_E_* code;
+ *    psr_last_error() returns a thread-local message for the last failure. No C++
+ *    exception crosses this interface.
+ *  - Units are CGS: mass fractions, K, s, dyn/cm^2, mol/cm^3.
+ *  - Batch arrays are row-major: [B][K] for species arrays (one contiguous row per
+ *    reactor), [B] for per-reactor scalars, [B][K+1][K+1] for Jacobians.
+ *  - Unless a function says otherwise, pointers are DEVICE pointers owned by the
+ *    caller, and the work is queued on the given CUDA stream (NULL = legacy default
+ *    stream) without synchronising; results are valid once the stream reaches them.
+ *  - Per-reactor outcomes (convergence failures) are reported in status[], never as a
+ *    call error. Call errors are argument errors, CUDA errors and allocation failures.
+ */
+#ifndef PSR_H
+#define PSR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* call status */
+#define PSR_OK 0
+#define PSR_E_ARG (-1)      /* invalid argument (null pointer, size, option value) */
+#define PSR_E_IO (-2)       /* mechanism file cannot be read */
+#define PSR_E_FORMAT (-3)   /* mechanism text malformed */
+#define PSR_E_CUDA (-4)     /* CUDA runtime error (message in psr_last_error) */
+#define PSR_E_OOM (-5)      /* device or host allocation failed */
+#define PSR_E_UNSUPPORTED (-6) /* valid input this build does not handle (e.g. too many species) */
+
+/* per-reactor status written to status[] */
+#define PSR_CONVERGED 0     /* ||F||_inf <= ftol and the last Newton step met the polish tolerance */
+#define PSR_MAX_ITER 1      /* max_newton Newton iterations used */
+#define PSR_NONFINITE 2     /* the residual at the initial guess is not finite */
+#define PSR_TS_EXHAUSTED 4  /* max_ts_rounds time-stepping rounds, or dt collapsed */
+
+/* precision of the Jacobian and its LU factors (the residual is always FP64) */
+#define PSR_FP64 0
+#define PSR_MIXED 1         /* FP32 Jacobian, FP32 LU; FP64 residual and Newton update */
+
+/* energy equation */
+#define PSR_ADIABATIC 0     /* Eq. (3) with Q = 0, dP/dt = 0 */
+#define PSR_FIXED_T 1       /* reactor temperature fixed at T0 (the paper's runs, Secs. 5-6) */
+
+typedef struct psr_mech psr_mech; /* opaque; owns host and device copies of the tables */
+
+typedef struct {
+    int32_t K;              /* species */
+    int32_t I;              /* reactions */
+    int32_t n_elements;
+    int32_t n_third_body;   /* reactions with a [M] factor */
+    int32_t n_falloff;      /* Troe falloff reactions */
+    int32_t has_soot;       /* the mechanism carries MOMIC soot constants */
+} psr_mech_info;
+
+/* Load a `.psrmech` text mechanism (format in the generator's documentation) from a
+ * file, or from `nbytes` bytes of text in host memory. On success *out owns host and
+ * device tables on the current CUDA device; free with psr_mech_free. Errors:
+ * PSR_E_IO, PSR_E_FORMAT (message names the offending record), PSR_E_CUDA, PSR_E_OOM. */
+int psr_mech_load(const char *path, psr_mech **out);
+int psr_mech_load_mem(const char *text, size_t nbytes, psr_mech **out);
+int psr_mech_info_get(const psr_mech *m, psr_mech_info *out);
+/* Host copies: species molecular weights W [K] (g/mol) and element counts [K][n_elements]. */
+int psr_mech_weights(const psr_mech *m, double *W_out);
+void psr_mech_free(psr_mech *m); /* NULL-safe */
+
+/* Solver controls. psr_options_default fills the defaults noted here. */
+typedef struct {
+    double ftol;            /* 1e-8: ||F||_inf target (F_k dimensionless, F_T = N/(c_p T)) */
+    double step_rtol;       /* 1e-10: polish: |dx_j| <= step_rtol |x_j| + atol_j on the last step */
+    double step_atol_y;     /* 1e-14 */
+    double step_atol_t;     /* 1e-10 K */
+    double ts_rtol;         /* 1e-4: a pseudo-time step is solved when |dx_j| <= ts_rtol |x_j| + ts_atol_j */
+    double ts_atol_y;       /* 1e-10 (temperature uses ts_rtol) */
+    double dt0_over_tau;    /* 1e-10: first pseudo-time step / tau */
+    double dt_shrink;       /* 0.25: dt factor after a failed pseudo-time step */
+    double y_floor;         /* 1e-10: iterates keep Y_k >= -y_floor */
+    double t_min, t_max;    /* 200 K, 5000 K: temperature bounds of the iterates */
+    int32_t max_newton;     /* 500: Newton iterations (steady and inside pseudo-time steps) */
+    int32_t max_damp;       /* 8: halvings of the damping factor */
+    int32_t max_ts_rounds;  /* 100: Newton attempts followed by time stepping */
+    int32_t ts_steps;       /* 12: pseudo-time steps per round */
+    int32_t ts_newton;      /* 8: Newton iterations per pseudo-time step */
+    int32_t precision;      /* PSR_FP64 (default) or PSR_MIXED */
+    int32_t energy;         /* PSR_ADIABATIC (default) or PSR_FIXED_T */
+    int32_t warps_per_block;/* 0 = tuned default */
+    int32_t blocks_per_sm;  /* 0 = as many as fit */
+    int32_t reserved[7];
+} psr_options;
+
+void psr_options_default(psr_options *o);
+
+/* Solve B independent steady PSRs (Sec. 2 Eqs. (1)-(3), Sec. 3 Eqs. (4)-(9); hybrid
+ * Newton / pseudo-transient iteration of Sec. 3).
+ *   Y_in [B][K], T_in [B], tau [B] (s, > 0), P [B] (dyn/cm^2, > 0): inlets.
+ *   Y0 [B][K], T0 [B]: initial guesses (T0 is the fixed temperature in PSR_FIXED_T).
+ *   rate_mult [I] or NULL: multiplier applied to every rate of progress q_i (all ones
+ *     when NULL); the sensitivity parameter of the adjoint is ln(rate_mult_i).
+ *   Y_out [B][K], T_out [B]: final iterates (the root for PSR_CONVERGED reactors).
+ *   iters [B], ts_steps [B], status [B], fnorm [B] (||F||_inf at the output state),
+ *   nfev [B] (residual evaluations, the reactor's share of the FP64 work): each may be NULL.
+ * One persistent kernel launch; reactors are taken from a work queue by warps.
+ * Device memory: a small work-queue counter is allocated and freed on the stream.
+ * Errors: PSR_E_ARG, PSR_E_UNSUPPORTED (K + 1 > 64 for this kernel), PSR_E_CUDA. */
+int psr_batch_solve(const psr_mech *m, int64_t B,
+                    const double *Y_in, const double *T_in, const double *tau, const double *P,
+                    const double *Y0, const double *T0, const double *rate_mult,
+                    double *Y_out, double *T_out,
+                    int32_t *iters, int32_t *ts_steps, int32_t *status, double *fnorm,
+                    int32_t *nfev, const psr_options *opt, void *cuda_stream);
+
+/* Same as psr_batch_solve with every array in HOST memory: the call copies the inputs
+ * to the device, solves, copies the outputs back and synchronises the stream before
+ * returning. Device buffers are allocated and freed inside the call. */
+int psr_batch_solve_host(const psr_mech *m, int64_t B,
+                         const double *Y_in, const double *T_in, const double *tau, const double *P,
+                         const double *Y0, const double *T0, const double *rate_mult,
+                         double *Y_out, double *T_out,
+                         int32_t *iters, int32_t *ts_steps, int32_t *status, double *fnorm,
+                         int32_t *nfev, const psr_options *opt, void *cuda_stream);
+
+/* Steady residual F(x) (Sec. 2 Eqs. (2)-(3) at d/dt = 0 with Eqs. (4)-(9)) at B states
+ * x = (Y [B][K], T [B]) for the given inlets: F_out [B][K+1], row b = (F_1..F_K, F_T)
+ * with F_k = Y_k - Y_k,in - tau wdot_k W_k / rho and
+ * F_T = [sum_k Y_k,in (h_k(T) - h_k(T_in)) + (tau/rho) sum_k h_k W_k wdot_k] / (c_p T)
+ * (adiabatic) or T - T0 (fixed T, T0 taken from T). Errors: PSR_E_ARG, PSR_E_CUDA. */
+int psr_eval_residual(const psr_mech *m, int64_t B,
+                      const double *Y_in, const double *T_in, const double *tau, const double *P,
+                      const double *Y, const double *T, const double *rate_mult,
+                      double *F_out, int32_t energy, void *cuda_stream);
+
+/* Analytic Jacobian dF/dx of psr_eval_residual at the same states, row-major
+ * J_out [B][K+1][K+1] in FP64 (precision PSR_FP64) or FP64-stored values of the FP32
+ * assembly (PSR_MIXED), exactly as the solver's Newton iteration uses them. */
+int psr_eval_jacobian(const psr_mech *m, int64_t B,
+                      const double *Y_in, const double *T_in, const double *tau, const double *P,
+                      const double *Y, const double *T, const double *rate_mult,
+                      double *J_out, int32_t energy, int32_t precision, void *cuda_stream);
+
+/* Batched dense solve A_b x_b = r_b by the solver's LU with partial pivoting
+ * (Sec. 1, Sec. 3): A [B][n][n] row-major, r [B][n], x_out [B][n], ok_out [B]
+ * (1 = factored, 0 = zero or non-finite pivot), n <= 64. PSR_MIXED factors in FP32. */
+int psr_batch_lu_solve(int64_t B, int32_t n, const double *A, const double *r,
+                       double *x_out, int32_t *ok_out, int32_t precision, void *cuda_stream);
+
+const char *psr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSR_H */

@@ -1,0 +1,402 @@
+// Mechanism loader: parses `.psrmech` text, derives the tables the kernels read and
+// uploads them to the current device in one allocation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <sstream>
+
+#include "psr_internal.h"
+
+namespace psr {
+
+static thread_local std::string g_err;
+
+int set_error(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_error(const char *what, int err) {
+    return set_error(PSR_E_CUDA, std::string(what) + ": " +
+                                     cudaGetErrorString(static_cast<cudaError_t>(err)));
+}
+
+namespace {
+
+struct Lines {
+    std::vector<std::vector<std::string>> rows;
+    size_t pos = 0;
+    bool next(std::vector<std::string> &r) {
+        if (pos >= rows.size()) return false;
+        r = rows[pos++];
+        return true;
+    }
+};
+
+bool to_d(const std::string &s, double &v) {
+    char *end = nullptr;
+    v = std::strtod(s.c_str(), &end);
+    return end && *end == '\0' && std::isfinite(v);
+}
+bool to_i(const std::string &s, long &v) {
+    char *end = nullptr;
+    v = std::strtol(s.c_str(), &end, 10);
+    return end && *end == '\0';
+}
+
+int parse(const std::string &text, Mech &m) {
+    Lines L;
+    std::istringstream in(text);
+    std::string line;
+    while (std::getline(in, line)) {
+        std::istringstream ls(line);
+        std::vector<std::string> toks;
+        std::string t;
+        while (ls >> t) toks.push_back(t);
+        if (toks.empty() || toks[0][0] == '#') continue;
+        L.rows.push_back(toks);
+    }
+    std::vector<std::string> r;
+    auto bad = [&](const std::string &what) {
+        return set_error(PSR_E_FORMAT, "psrmech: " + what);
+    };
+    if (!L.next(r) || r.size() < 2 || r[0] != "psrmech" || r[1] != "1") return bad("missing 'psrmech 1' header");
+    long E = 0, K = 0, I = 0, v = 0;
+    if (!L.next(r) || r.size() != 2 || r[0] != "elements" || !to_i(r[1], E) || E < 1 || E > 16)
+        return bad("bad 'elements' record");
+    m.E = static_cast<int>(E);
+    for (long e = 0; e < E; ++e) {
+        double w;
+        if (!L.next(r) || r.size() != 2 || !to_d(r[1], w) || w <= 0) return bad("bad element record");
+        m.elem_w.push_back(w);
+    }
+    if (!L.next(r) || r.size() != 2 || r[0] != "species" || !to_i(r[1], K) || K < 1 || K > 30000)
+        return bad("bad 'species' record");
+    m.K = static_cast<int>(K);
+    m.comp.assign(K * E, 0.0);
+    m.nasa.assign(K * 16, 0.0);
+    m.W.assign(K, 0.0);
+    for (long k = 0; k < K; ++k) {
+        if (!L.next(r) || (long)r.size() != 2 + E + 3 + 14 || !to_i(r[0], v) || v != k)
+            return bad("bad species record " + std::to_string(k));
+        double w = 0;
+        for (long e = 0; e < E; ++e) {
+            double a;
+            if (!to_d(r[2 + e], a) || a < 0) return bad("bad composition of species " + std::to_string(k));
+            m.comp[k * E + e] = a;
+            w += a * m.elem_w[e];
+        }
+        if (w <= 0) return bad("species " + std::to_string(k) + " has no atoms");
+        m.W[k] = w;
+        double vals[17];
+        for (int j = 0; j < 17; ++j)
+            if (!to_d(r[2 + E + j], vals[j])) return bad("bad thermo of species " + std::to_string(k));
+        m.nasa[k * 16 + 0] = vals[1];                   // T_mid
+        for (int j = 0; j < 7; ++j) m.nasa[k * 16 + 1 + j] = vals[3 + j];    // low range
+        for (int j = 0; j < 7; ++j) m.nasa[k * 16 + 8 + j] = vals[10 + j];   // high range
+    }
+    if (!L.next(r) || r.size() != 2 || r[0] != "reactions" || !to_i(r[1], I) || I < 1 || I > 32767)
+        return bad("bad 'reactions' record");
+    m.I = static_cast<int>(I);
+    m.slots.assign(I * 6, static_cast<int16_t>(K));
+    m.dnu.assign(I, 0);
+    m.type.assign(I, kElem);
+    m.lnA.assign(I, 0.0);
+    m.beta.assign(I, 0.0);
+    m.theta.assign(I, 0.0);
+    m.troe_row.assign(I, -1);
+    m.eff_ptr.assign(I + 1, 0);
+    std::vector<std::vector<std::pair<int, double>>> effs(I);
+    for (long i = 0; i < I; ++i) {
+        if (!L.next(r) || r.size() < 4 || !to_i(r[0], v) || v != i)
+            return bad("bad reaction record " + std::to_string(i));
+        const std::string &kind = r[1];
+        if (kind == "elem") m.type[i] = kElem;
+        else if (kind == "tb") m.type[i] = kThirdBody;
+        else if (kind == "troe") m.type[i] = kTroe;
+        else return bad("unknown reaction type '" + kind + "'");
+        size_t p = 2;
+        int dn = 0;
+        for (int side = 0; side < 2; ++side) {
+            long n;
+            if (p >= r.size() || !to_i(r[p], n) || n < 1 || n > 3)
+                return bad("reaction " + std::to_string(i) + ": 1..3 species per side");
+            ++p;
+            for (long s = 0; s < n; ++s) {
+                long sp;
+                if (p >= r.size() || !to_i(r[p], sp) || sp < 0 || sp >= K)
+                    return bad("reaction " + std::to_string(i) + ": bad species index");
+                m.slots[i * 6 + side * 3 + s] = static_cast<int16_t>(sp);
+                dn += side ? 1 : -1;
+                ++p;
+            }
+        }
+        m.dnu[i] = static_cast<int8_t>(dn);
+        double A, b, th;
+        if (p + 3 > r.size() || !to_d(r[p], A) || !to_d(r[p + 1], b) || !to_d(r[p + 2], th) || A <= 0)
+            return bad("reaction " + std::to_string(i) + ": bad Arrhenius parameters");
+        m.lnA[i] = std::log(A);
+        m.beta[i] = b;
+        m.theta[i] = th;
+        p += 3;
+        double low[3] = {0, 0, 0}, troe[4] = {0, 0, 0, 0};
+        bool has_low = false, has_troe = false;
+        while (p < r.size()) {
+            if (r[p] == "low" && p + 3 < r.size()) {
+                for (int j = 0; j < 3; ++j)
+                    if (!to_d(r[p + 1 + j], low[j])) return bad("reaction " + std::to_string(i) + ": bad low");
+                if (low[0] <= 0) return bad("reaction " + std::to_string(i) + ": A0 <= 0");
+                has_low = true;
+                p += 4;
+            } else if (r[p] == "troe" && p + 4 < r.size()) {
+                for (int j = 0; j < 4; ++j)
+                    if (!to_d(r[p + 1 + j], troe[j])) return bad("reaction " + std::to_string(i) + ": bad troe");
+                has_troe = true;
+                p += 5;
+            } else if (r[p] == "eff" && p + 1 < r.size()) {
+                long ne;
+                if (!to_i(r[p + 1], ne) || ne < 0 || ne > K) return bad("reaction " + std::to_string(i) + ": bad eff");
+                p += 2;
+                for (long e = 0; e < ne; ++e) {
+                    long sp;
+                    double ev;
+                    if (p + 1 >= r.size() || !to_i(r[p], sp) || sp < 0 || sp >= K || !to_d(r[p + 1], ev) || ev < 0)
+                        return bad("reaction " + std::to_string(i) + ": bad efficiency");
+                    effs[i].push_back({static_cast<int>(sp), ev - 1.0});
+                    p += 2;
+                }
+            } else {
+                return bad("reaction " + std::to_string(i) + ": unknown field '" + r[p] + "'");
+            }
+        }
+        if (m.type[i] == kTroe) {
+            if (!has_low || !has_troe) return bad("falloff reaction " + std::to_string(i) + " needs low and troe");
+            if (troe[1] <= 0 || troe[2] <= 0) return bad("falloff reaction " + std::to_string(i) + ": T3, T1 > 0");
+            m.troe_row[i] = m.n_troe++;
+            m.troe.insert(m.troe.end(), {std::log(low[0]), low[1], low[2], troe[0], troe[1], troe[2], troe[3], 0.0});
+        } else if (has_low || has_troe) {
+            return bad("reaction " + std::to_string(i) + ": low/troe on a non-falloff reaction");
+        }
+        if (m.type[i] == kThirdBody) m.n_tb++;
+        if (m.type[i] == kElem && !effs[i].empty()) return bad("reaction " + std::to_string(i) + ": eff on elementary");
+    }
+    while (L.next(r)) {
+        if (r[0] == "soot") {
+            m.has_soot = true;
+            for (size_t j = 1; j + 1 < r.size(); j += 2) {
+                double x;
+                if (!to_d(r[j + 1], x)) return bad("bad soot constant '" + r[j] + "'");
+                m.soot_keys.push_back(r[j]);
+                m.soot.push_back(x);
+            }
+        } else if (r[0] == "end") {
+            break;
+        } else {
+            return bad("unexpected record '" + r[0] + "'");
+        }
+    }
+    // efficiency CSR
+    for (long i = 0; i < I; ++i) {
+        m.eff_ptr[i + 1] = m.eff_ptr[i] + static_cast<int32_t>(effs[i].size());
+        for (auto &e : effs[i]) {
+            m.eff_sp.push_back(static_cast<int16_t>(e.first));
+            m.eff_val.push_back(e.second);
+        }
+    }
+    // distinct participants and net stoichiometry; species -> reaction CSR (Eq. (4))
+    m.part.assign(I * 6, static_cast<int16_t>(K));
+    m.part_nu.assign(I * 6, 0);
+    std::vector<std::vector<std::pair<int, int>>> by_sp(K);
+    for (long i = 0; i < I; ++i) {
+        std::map<int, int> nu;
+        for (int s = 0; s < 6; ++s) {
+            int sp = m.slots[i * 6 + s];
+            if (sp < K) nu[sp] += (s < 3) ? -1 : 1;
+        }
+        int j = 0;
+        for (auto &kv : nu) {
+            m.part[i * 6 + j] = static_cast<int16_t>(kv.first);
+            m.part_nu[i * 6 + j] = static_cast<int8_t>(kv.second);
+            ++j;
+            if (kv.second != 0) by_sp[kv.first].push_back({static_cast<int>(i), kv.second});
+        }
+    }
+    m.sp_ptr.assign(K + 1, 0);
+    for (long k = 0; k < K; ++k) {
+        m.sp_ptr[k + 1] = m.sp_ptr[k] + static_cast<int32_t>(by_sp[k].size());
+        for (auto &e : by_sp[k]) {
+            m.sp_rxn.push_back(static_cast<int16_t>(e.first));
+            m.sp_nu.push_back(static_cast<int8_t>(e.second));
+        }
+    }
+    return PSR_OK;
+}
+
+template <class T>
+void place(std::vector<char> &blob, const std::vector<T> &v, size_t &off_out) {
+    size_t off = (blob.size() + 255) & ~size_t(255);
+    blob.resize(off + v.size() * sizeof(T) + 1);
+    if (!v.empty()) std::memcpy(blob.data() + off, v.data(), v.size() * sizeof(T));
+    off_out = off;
+}
+
+int upload(Mech &m) {
+    std::vector<char> blob;
+    std::vector<double> invW(m.K);
+    for (int k = 0; k < m.K; ++k) invW[k] = 1.0 / m.W[k];
+    size_t oW, oinvW, onasa, olnA, obeta, otheta, oslots, odnu, otype, oeffp, oeffs, oeffv, otr, otroe,
+        osp, ospr, ospn, opart, opartnu;
+    place(blob, m.W, oW);
+    place(blob, invW, oinvW);
+    place(blob, m.nasa, onasa);
+    place(blob, m.lnA, olnA);
+    place(blob, m.beta, obeta);
+    place(blob, m.theta, otheta);
+    place(blob, m.slots, oslots);
+    place(blob, m.dnu, odnu);
+    place(blob, m.type, otype);
+    place(blob, m.eff_ptr, oeffp);
+    place(blob, m.eff_sp, oeffs);
+    place(blob, m.eff_val, oeffv);
+    place(blob, m.troe_row, otr);
+    place(blob, m.troe, otroe);
+    place(blob, m.sp_ptr, osp);
+    place(blob, m.sp_rxn, ospr);
+    place(blob, m.sp_nu, ospn);
+    place(blob, m.part, opart);
+    place(blob, m.part_nu, opartnu);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error("cudaGetDevice", e);
+    void *d = nullptr;
+    e = cudaMalloc(&d, blob.size());
+    if (e != cudaSuccess) return set_error(PSR_E_OOM, "cudaMalloc of mechanism tables failed");
+    e = cudaMemcpy(d, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_error("cudaMemcpy mechanism", e);
+    }
+    char *b = static_cast<char *>(d);
+    m.device = dev;
+    m.dev_block = d;
+    DevMech &D = m.dev;
+    D.K = m.K;
+    D.I = m.I;
+    D.n_troe = m.n_troe;
+    D.n_eff = static_cast<int>(m.eff_sp.size());
+    D.W = reinterpret_cast<const double *>(b + oW);
+    D.invW = reinterpret_cast<const double *>(b + oinvW);
+    D.nasa = reinterpret_cast<const double *>(b + onasa);
+    D.lnA = reinterpret_cast<const double *>(b + olnA);
+    D.beta = reinterpret_cast<const double *>(b + obeta);
+    D.theta = reinterpret_cast<const double *>(b + otheta);
+    D.slots = reinterpret_cast<const int16_t *>(b + oslots);
+    D.dnu = reinterpret_cast<const int8_t *>(b + odnu);
+    D.type = reinterpret_cast<const int8_t *>(b + otype);
+    D.eff_ptr = reinterpret_cast<const int32_t *>(b + oeffp);
+    D.eff_sp = reinterpret_cast<const int16_t *>(b + oeffs);
+    D.eff_val = reinterpret_cast<const double *>(b + oeffv);
+    D.troe_row = reinterpret_cast<const int32_t *>(b + otr);
+    D.troe = reinterpret_cast<const double *>(b + otroe);
+    D.sp_ptr = reinterpret_cast<const int32_t *>(b + osp);
+    D.sp_rxn = reinterpret_cast<const int16_t *>(b + ospr);
+    D.sp_nu = reinterpret_cast<const int8_t *>(b + ospn);
+    D.part = reinterpret_cast<const int16_t *>(b + opart);
+    D.part_nu = reinterpret_cast<const int8_t *>(b + opartnu);
+    return PSR_OK;
+}
+
+int load_text(const std::string &text, psr_mech **out) {
+    if (!out) return set_error(PSR_E_ARG, "psr_mech_load: out is NULL");
+    *out = nullptr;
+    auto *pm = new (std::nothrow) psr_mech();
+    if (!pm) return set_error(PSR_E_OOM, "host allocation failed");
+    int rc = parse(text, pm->m);
+    if (rc == PSR_OK) rc = upload(pm->m);
+    if (rc != PSR_OK) {
+        delete pm;
+        return rc;
+    }
+    *out = pm;
+    return PSR_OK;
+}
+
+}  // namespace
+}  // namespace psr
+
+extern "C" {
+
+int psr_mech_load(const char *path, psr_mech **out) {
+    if (!path) return psr::set_error(PSR_E_ARG, "psr_mech_load: path is NULL");
+    std::ifstream f(path, std::ios::binary);
+    if (!f) return psr::set_error(PSR_E_IO, std::string("cannot open ") + path);
+    std::stringstream ss;
+    ss << f.rdbuf();
+    return psr::load_text(ss.str(), out);
+}
+
+int psr_mech_load_mem(const char *text, size_t nbytes, psr_mech **out) {
+    if (!text) return psr::set_error(PSR_E_ARG, "psr_mech_load_mem: text is NULL");
+    return psr::load_text(std::string(text, nbytes), out);
+}
+
+int psr_mech_info_get(const psr_mech *m, psr_mech_info *out) {
+    if (!m || !out) return psr::set_error(PSR_E_ARG, "psr_mech_info_get: NULL argument");
+    out->K = m->m.K;
+    out->I = m->m.I;
+    out->n_elements = m->m.E;
+    out->n_third_body = m->m.n_tb;
+    out->n_falloff = m->m.n_troe;
+    out->has_soot = m->m.has_soot ? 1 : 0;
+    return PSR_OK;
+}
+
+int psr_mech_weights(const psr_mech *m, double *W_out) {
+    if (!m || !W_out) return psr::set_error(PSR_E_ARG, "psr_mech_weights: NULL argument");
+    std::memcpy(W_out, m->m.W.data(), sizeof(double) * m->m.K);
+    return PSR_OK;
+}
+
+void psr_mech_free(psr_mech *m) {
+    if (!m) return;
+    if (m->m.dev_block) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != m->m.device && m->m.device >= 0) cudaSetDevice(m->m.device);
+        cudaFree(m->m.dev_block);
+        if (cur >= 0 && cur != m->m.device) cudaSetDevice(cur);
+    }
+    delete m;
+}
+
+const char *psr_last_error(void) { return psr::g_err.c_str(); }
+
+void psr_options_default(psr_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->ftol = 1e-8;
+    o->step_rtol = 1e-10;
+    o->step_atol_y = 1e-14;
+    o->step_atol_t = 1e-10;
+    o->ts_rtol = 1e-4;
+    o->ts_atol_y = 1e-10;
+    o->dt0_over_tau = 1e-10;
+    o->dt_shrink = 0.25;
+    o->y_floor = 1e-10;
+    o->t_min = 200.0;
+    o->t_max = 5000.0;
+    o->max_newton = 500;
+    o->max_damp = 8;
+    o->max_ts_rounds = 100;
+    o->ts_steps = 12;
+    o->ts_newton = 8;
+    o->precision = PSR_FP64;
+    o->energy = PSR_ADIABATIC;
+}
+
+}  // extern "C"

@@ -1,0 +1,70 @@
+// Internal declarations of libpsr shared by the mechanism loader and the kernels.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "psr.h"
+
+namespace psr {
+
+constexpr double kRu = 8.314462618e7;   // erg / (mol K)
+constexpr double kPatm = 1.01325e6;     // dyn / cm^2, standard state of Eq. (8)
+constexpr int kMaxWarpN = 64;           // K + 1 handled by one warp (two rows per lane)
+
+enum RxnType : int8_t { kElem = 0, kThirdBody = 1, kTroe = 2 };
+
+// Device-side view of a mechanism: structure-of-arrays tables, all device pointers.
+struct DevMech {
+    int K, I, n_troe, n_eff;
+    const double *W, *invW;      // [K] g/mol
+    const double *nasa;          // [K][16]: T_mid, low a1..a7, high a1..a7, 0
+    const double *lnA, *beta, *theta;   // [I] Eq. (6), E/R in K
+    const int16_t *slots;        // [I][6] reactant slots 0..2, product slots 3..5, K = empty
+    const int8_t *dnu;           // [I] sum_k nu_ki
+    const int8_t *type;          // [I] RxnType
+    const int32_t *eff_ptr;      // [I+1] CSR of (efficiency - 1) for tb/troe rows
+    const int16_t *eff_sp;       // [n_eff]
+    const double *eff_val;       // [n_eff] eps - 1
+    const int32_t *troe_row;     // [I] row of troe params or -1
+    const double *troe;          // [n_troe][8]: ln A0, beta0, E0/R, alpha, T3, T1, T2, 0
+    const int32_t *sp_ptr;       // [K+1] CSR species -> reactions for wdot_k = sum nu_ki q_i
+    const int16_t *sp_rxn;
+    const int8_t *sp_nu;
+    const int16_t *part;         // [I][6] distinct participants (K = none)
+    const int8_t *part_nu;       // [I][6] net nu of each participant
+};
+
+struct Mech {
+    int K = 0, I = 0, E = 0, n_tb = 0, n_troe = 0;
+    bool has_soot = false;
+    std::vector<double> elem_w, W, comp;       // comp [K][E]
+    std::vector<double> nasa;                  // [K][16]
+    std::vector<double> lnA, beta, theta;
+    std::vector<int16_t> slots;                // [I][6]
+    std::vector<int8_t> dnu, type;
+    std::vector<int32_t> eff_ptr;
+    std::vector<int16_t> eff_sp;
+    std::vector<double> eff_val;
+    std::vector<int32_t> troe_row;
+    std::vector<double> troe;
+    std::vector<int32_t> sp_ptr;
+    std::vector<int16_t> sp_rxn;
+    std::vector<int8_t> sp_nu;
+    std::vector<int16_t> part;
+    std::vector<int8_t> part_nu;
+    std::vector<double> soot;                  // raw soot constants (key order of the file)
+    std::vector<std::string> soot_keys;
+    int device = -1;
+    void *dev_block = nullptr;                 // one device allocation for all tables
+    DevMech dev{};
+};
+
+int set_error(int code, const std::string &msg);
+int cuda_error(const char *what, int err);
+
+}  // namespace psr
+
+struct psr_mech {
+    psr::Mech m;
+};

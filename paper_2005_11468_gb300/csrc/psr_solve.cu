@@ -1,0 +1,1175 @@
+// Batched steady PSR solve on sm_103a: one warp per reactor, persistent work queue.
+//
+// Per reactor the warp runs the hybrid scheme of Sec. 3: damped Newton on the steady
+// residual of Eqs. (2)-(3) (with Eqs. (4)-(9) for the rates), and, when Newton fails,
+// backward-Euler pseudo-time steps of the transient balances (each solved by damped
+// Newton) before Newton is tried again. State vectors live in registers (lane j owns
+// components j and j + 32), species-indexed tables and the Jacobian in shared memory.
+// The residual is always FP64; the Jacobian and its LU are FP64 (PSR_FP64) or FP32
+// (PSR_MIXED), in which case Newton on the FP64 residual refines the FP32 solves.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "psr_internal.h"
+
+namespace psr {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr double kLn10 = 2.302585092994045684;
+
+// ---------------------------------------------------------------- warp helpers
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+__device__ __forceinline__ double wmax(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+__device__ __forceinline__ double wmin(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+// A length-n vector distributed over the warp: lane l holds components l and l + 32.
+struct V2 {
+    double a, b;
+};
+__device__ __forceinline__ double comp_get(const V2 &v, int j) {
+    double x = __shfl_sync(kFull, j < 32 ? v.a : v.b, j & 31);
+    return x;
+}
+
+// ---------------------------------------------------------------- per-call parameters
+struct Batch {
+    int64_t B;
+    const double *Y_in, *T_in, *tau, *P, *Y0, *T0, *rate_mult;
+    double *Y_out, *T_out, *fnorm;
+    int32_t *iters, *ts_steps, *status, *nfev;
+};
+
+struct Opts {
+    double ftol, step_rtol, step_atol_y, step_atol_t, ts_rtol, ts_atol_y, dt0_over_tau, dt_shrink,
+        y_floor, t_min, t_max;
+    int max_newton, max_damp, max_ts_rounds, ts_steps, ts_newton, energy;
+};
+
+// Per-warp shared-memory workspace.
+template <class TJ>
+struct WS {
+    double *C, *hRT, *gS;    // [K+1]: concentrations (C[K] = 1), H/RT, S/R - H/RT (sentinels 0)
+    double *kf, *kr, *q;     // [I]: effective rate constants of the last residual, q_i (or Euler sums)
+    double *v;               // [K] dense third-body column part of the concentration Jacobian
+    TJ *J;                   // [n][P]
+    TJ *rhs;                 // [n]
+    int16_t *perm;           // [n] row order after pivoting
+    int P;                   // row pitch of J (elements)
+};
+
+template <class TJ>
+__host__ __device__ inline size_t ws_bytes(int K, int I, int n) {
+    int P = n + 1;
+    size_t b = sizeof(double) * (3 * (K + 1) + 3 * I + K);
+    b = (b + 15) & ~size_t(15);
+    b += sizeof(TJ) * (size_t(n) * P + n);
+    b = (b + 15) & ~size_t(15);
+    b += sizeof(int16_t) * n;
+    return (b + 15) & ~size_t(15);
+}
+
+template <class TJ>
+__device__ WS<TJ> carve(char *base, int K, int I, int n) {
+    WS<TJ> w;
+    double *d = reinterpret_cast<double *>(base);
+    w.C = d;
+    w.hRT = d + (K + 1);
+    w.gS = d + 2 * (K + 1);
+    w.kf = d + 3 * (K + 1);
+    w.kr = w.kf + I;
+    w.q = w.kr + I;
+    w.v = w.q + I;
+    size_t off = sizeof(double) * (3 * (K + 1) + 3 * I + K);
+    off = (off + 15) & ~size_t(15);
+    w.P = n + 1;
+    w.J = reinterpret_cast<TJ *>(base + off);
+    w.rhs = w.J + size_t(n) * w.P;
+    off += sizeof(TJ) * (size_t(n) * w.P + n);
+    off = (off + 15) & ~size_t(15);
+    w.perm = reinterpret_cast<int16_t *>(base + off);
+    return w;
+}
+
+// Scalars of the last residual evaluation that the Jacobian reuses.
+struct Mix {
+    double T, lnT, invT, rho, Wbar, Ctot, lnPRT;
+    double N, cp, sum_yin_cp, sum_y_dcp;     // energy row pieces
+    double h_in;                             // sum_k Y_k,in h_k(T_in), per reactor
+};
+
+// Lane-owned species data of the last residual evaluation.
+struct SpecLane {
+    double cpR[2], dcpR[2];
+};
+
+// ---------------------------------------------------------------- thermo (NASA-7)
+__device__ __forceinline__ void nasa7(const double *__restrict__ nasa, int k, double T, double lnT,
+                                      double &cpR, double &hRT, double &sR, double &dcpR) {
+    const double *c = nasa + size_t(k) * 16;
+    const double tmid = __ldg(c);
+    const double *a = c + (T < tmid ? 1 : 8);
+    const double a1 = __ldg(a), a2 = __ldg(a + 1), a3 = __ldg(a + 2), a4 = __ldg(a + 3), a5 = __ldg(a + 4),
+                 a6 = __ldg(a + 5), a7 = __ldg(a + 6);
+    cpR = a1 + T * (a2 + T * (a3 + T * (a4 + T * a5)));
+    hRT = a1 + T * (a2 / 2 + T * (a3 / 3 + T * (a4 / 4 + T * a5 / 5))) + a6 / T;
+    sR = a1 * lnT + T * (a2 + T * (a3 / 2 + T * (a4 / 3 + T * a5 / 4))) + a7;
+    dcpR = a2 + T * (2 * a3 + T * (3 * a4 + T * 4 * a5));
+}
+
+// ---------------------------------------------------------------- Troe falloff pieces
+struct Troe {
+    double fac;       // P_r / (1 + P_r) F
+    double D;         // d ln(fac) / d ln P_r
+    double dlnF_dT;   // d ln F / dT at fixed P_r
+    double dlk0;      // d ln k0 / dT
+};
+
+__device__ __forceinline__ Troe troe_eval(const double *__restrict__ tp, double a_inf, double M, double T,
+                                          double lnT, double invT, bool want_deriv) {
+    Troe t;
+    const double lnA0 = __ldg(tp), b0 = __ldg(tp + 1), th0 = __ldg(tp + 2), al = __ldg(tp + 3),
+                 T3 = __ldg(tp + 4), T1 = __ldg(tp + 5), T2 = __ldg(tp + 6);
+    const double Pr = exp(lnA0 + b0 * lnT - th0 * invT - a_inf) * M;     // k0 [M] / k_inf
+    const double e3 = exp(-T / T3), e1 = exp(-T / T1);
+    const double e2 = (T2 != 0.0) ? exp(-T2 * invT) : 0.0;
+    const double Fc = (1.0 - al) * e3 + al * e1 + e2;
+    const double L = log10(Fc);
+    const double cc = -0.4 - 0.67 * L, nn = 0.75 - 1.27 * L;
+    const double u = log10(Pr) + cc;
+    const double den = nn - 0.14 * u;
+    const double f1 = u / den;
+    const double s = 1.0 + f1 * f1;
+    const double lgF = L / s;
+    const double F = exp(kLn10 * lgF);
+    t.fac = Pr / (1.0 + Pr) * F;
+    if (want_deriv) {
+        const double dlgF_du = -L * 2.0 * f1 / (s * s) * nn / (den * den);
+        t.D = 1.0 / (1.0 + Pr) + dlgF_du;
+        const double dFc = -(1.0 - al) / T3 * e3 - al / T1 * e1 + ((T2 != 0.0) ? T2 * invT * invT * e2 : 0.0);
+        const double dL_dT = dFc / (Fc * kLn10);
+        const double df1_dL = (-0.67 * nn + 1.27 * u) / (den * den);
+        const double dlgF_dL = 1.0 / s - L * 2.0 * f1 / (s * s) * df1_dL;
+        t.dlnF_dT = kLn10 * dlgF_dL * dL_dT;
+        t.dlk0 = b0 * invT + th0 * invT * invT;
+    } else {
+        t.D = t.dlnF_dT = t.dlk0 = 0.0;
+    }
+    return t;
+}
+
+// ---------------------------------------------------------------- residual, Eqs. (2)-(9)
+// Evaluates F at state y; leaves C, hRT, gS, kf, kr (effective) of this state in shared
+// memory and the scalars/lane data in mx/sl for the Jacobian.
+template <class TJ>
+__device__ void eval_F(const DevMech &M, const WS<TJ> &w, const V2 &y, V2 &F, Mix &mx, SpecLane &sl,
+                       const double *Yin_row, double tau, double P, double Tspec, int energy,
+                       const double *__restrict__ mult) {
+    const int lane = threadIdx.x & 31;
+    const int K = M.K, I = M.I;
+    const double T = comp_get(y, K);
+    const double lnT = log(T), invT = 1.0 / T;
+    mx.T = T;
+    mx.lnT = lnT;
+    mx.invT = invT;
+    // mixture: W_bar = 1 / sum Y/W, rho = P W_bar / (R T), [X_k] = rho Y_k / W_k
+    double sYW = 0.0;
+    for (int h = 0; h < 2; ++h) {
+        int j = lane + 32 * h;
+        if (j < K) sYW += (h ? y.b : y.a) * __ldg(M.invW + j);
+    }
+    sYW = wsum(sYW);
+    const double Wbar = 1.0 / sYW;
+    const double rho = P * Wbar / (kRu * T);
+    mx.Wbar = Wbar;
+    mx.rho = rho;
+    mx.Ctot = P / (kRu * T);
+    mx.lnPRT = log(kPatm / (kRu * T));
+    double s_yin_h = 0.0, s_cp = 0.0, s_yin_cp = 0.0, s_y_dcp = 0.0;
+    for (int h = 0; h < 2; ++h) {
+        int j = lane + 32 * h;
+        if (j < K) {
+            double Yj = h ? y.b : y.a;
+            double cpR, hRT, sR, dcpR;
+            nasa7(M.nasa, j, T, lnT, cpR, hRT, sR, dcpR);
+            const double invW = __ldg(M.invW + j);
+            w.C[j] = rho * Yj * invW;
+            w.hRT[j] = hRT;
+            w.gS[j] = sR - hRT;
+            sl.cpR[h] = cpR;
+            sl.dcpR[h] = dcpR;
+            const double yin = Yin_row[j];
+            s_yin_h += yin * hRT * invW;
+            s_cp += Yj * cpR * invW;
+            s_yin_cp += yin * cpR * invW;
+            s_y_dcp += Yj * dcpR * invW;
+        }
+    }
+    if (lane == 0) {
+        w.C[K] = 1.0;
+        w.hRT[K] = 0.0;
+        w.gS[K] = 0.0;
+    }
+    __syncwarp();
+    // rates of progress, Eqs. (5)-(9) with third-body and Troe forms
+    for (int i = lane; i < I; i += 32) {
+        const int16_t *sl6 = M.slots + size_t(i) * 6;
+        const int s0 = __ldg(sl6), s1 = __ldg(sl6 + 1), s2 = __ldg(sl6 + 2), s3 = __ldg(sl6 + 3),
+                  s4 = __ldg(sl6 + 4), s5 = __ldg(sl6 + 5);
+        const double a = __ldg(M.lnA + i) + __ldg(M.beta + i) * lnT - __ldg(M.theta + i) * invT;
+        const double lnKc = (w.gS[s3] + w.gS[s4] + w.gS[s5]) - (w.gS[s0] + w.gS[s1] + w.gS[s2]) +
+                            double(__ldg(M.dnu + i)) * mx.lnPRT;
+        double kf = exp(a), kr = exp(a - lnKc);
+        const int typ = __ldg(M.type + i);
+        double Mc = 1.0;
+        if (typ != kElem) {
+            Mc = mx.Ctot;
+            for (int e = __ldg(M.eff_ptr + i); e < __ldg(M.eff_ptr + i + 1); ++e)
+                Mc += __ldg(M.eff_val + e) * w.C[__ldg(M.eff_sp + e)];
+            if (typ == kTroe) {
+                Troe t = troe_eval(M.troe + size_t(__ldg(M.troe_row + i)) * 8, a, Mc, T, lnT, invT, false);
+                kf *= t.fac;
+                kr *= t.fac;
+            }
+        }
+        w.kf[i] = kf;
+        w.kr[i] = kr;
+        double q = kf * (w.C[s0] * w.C[s1] * w.C[s2]) - kr * (w.C[s3] * w.C[s4] * w.C[s5]);
+        if (typ == kThirdBody) q *= Mc;
+        if (mult) q *= __ldg(mult + i);
+        w.q[i] = q;
+    }
+    __syncwarp();
+    // Eq. (4) and the species residuals of Eq. (2); wdot_k is left in v[] for the Jacobian
+    double s_hw = 0.0;
+    F.a = 0.0;
+    F.b = 0.0;
+    for (int h = 0; h < 2; ++h) {
+        int j = lane + 32 * h;
+        if (j < K) {
+            double wd = 0.0;
+            for (int e = __ldg(M.sp_ptr + j); e < __ldg(M.sp_ptr + j + 1); ++e)
+                wd += double(__ldg(M.sp_nu + e)) * w.q[__ldg(M.sp_rxn + e)];
+            const double Yj = h ? y.b : y.a;
+            const double f = Yj - Yin_row[j] - tau * __ldg(M.W + j) * wd / rho;
+            s_hw += w.hRT[j] * wd;
+            if (h) F.b = f;
+            else F.a = f;
+            w.v[j] = wd;
+        }
+    }
+    s_yin_h = wsum(s_yin_h);
+    s_cp = wsum(s_cp);
+    s_yin_cp = wsum(s_yin_cp);
+    s_y_dcp = wsum(s_y_dcp);
+    s_hw = wsum(s_hw);
+    const double RT = kRu * T;
+    const double cp = s_cp * kRu;                                  // c_p,mix, erg/(g K)
+    const double N = s_yin_h * RT - mx.h_in + tau * RT * s_hw / rho;  // energy balance, erg/g
+    mx.N = N;
+    mx.cp = cp;
+    mx.sum_yin_cp = s_yin_cp * kRu;
+    mx.sum_y_dcp = s_y_dcp * kRu;
+    const double FT = (energy == PSR_FIXED_T) ? (T - Tspec) : N / (cp * T);
+    if (lane == (K & 31)) {
+        if (K < 32) F.a = FT;
+        else F.b = FT;
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------- Jacobian
+// Analytic dF/dx at the state of the last eval_F (whose C, hRT, gS, kf, kr, v=wdot and
+// mx/sl it reuses), plus diag(c). Written into w.J (rows/cols 0..n-1).
+template <class TJ>
+__device__ void eval_J(const DevMech &M, const WS<TJ> &w, const V2 &y, const V2 &c, const Mix &mx,
+                       const SpecLane &sl, const double *Yin_row, double tau, int energy,
+                       const double *__restrict__ mult) {
+    const int lane = threadIdx.x & 31;
+    const int K = M.K, I = M.I, n = K + 1, P = w.P;
+    // wdot (left in v[] by eval_F) moves to registers; v[] becomes the dense part
+    double wd[2];
+    for (int h = 0; h < 2; ++h) {
+        int j = lane + 32 * h;
+        wd[h] = (j < K) ? w.v[j] : 0.0;
+    }
+    __syncwarp();
+    for (int idx = lane; idx < n * P; idx += 32) w.J[idx] = TJ(0);
+    for (int j = lane; j < K; j += 32) w.v[j] = 0.0;
+    __syncwarp();
+    const double T = mx.T, invT = mx.invT;
+    for (int i = lane; i < I; i += 32) {
+        const int16_t *sl6 = M.slots + size_t(i) * 6;
+        int s[6];
+        double cs[6];
+#pragma unroll
+        for (int t = 0; t < 6; ++t) {
+            s[t] = __ldg(sl6 + t);
+            cs[t] = w.C[s[t]];
+        }
+        const double Pf = cs[0] * cs[1] * cs[2], Pr_ = cs[3] * cs[4] * cs[5];
+        double d[6];
+        d[0] = cs[1] * cs[2];
+        d[1] = cs[0] * cs[2];
+        d[2] = cs[0] * cs[1];
+        d[3] = cs[4] * cs[5];
+        d[4] = cs[3] * cs[5];
+        d[5] = cs[3] * cs[4];
+        const double kf = w.kf[i], kr = w.kr[i];
+        const double m = mult ? __ldg(mult + i) : 1.0;
+        const int typ = __ldg(M.type + i);
+        double Mc = 1.0;
+        if (typ != kElem) {
+            Mc = mx.Ctot;
+            for (int e = __ldg(M.eff_ptr + i); e < __ldg(M.eff_ptr + i + 1); ++e)
+                Mc += __ldg(M.eff_val + e) * w.C[__ldg(M.eff_sp + e)];
+        }
+        const double sM = (typ == kThirdBody) ? Mc : 1.0;
+        const double dlkf = __ldg(M.beta + i) * invT + __ldg(M.theta + i) * invT * invT;
+        const double dlKc = ((w.hRT[s[3]] + w.hRT[s[4]] + w.hRT[s[5]]) - (w.hRT[s[0]] + w.hRT[s[1]] + w.hRT[s[2]])) *
+                                invT - double(__ldg(M.dnu + i)) * invT;
+        double dlkfe = dlkf, dqdM = 0.0;
+        if (typ == kThirdBody) {
+            dqdM = m * (kf * Pf - kr * Pr_);
+        } else if (typ == kTroe) {
+            const double a = __ldg(M.lnA + i) + __ldg(M.beta + i) * mx.lnT - __ldg(M.theta + i) * invT;
+            Troe t = troe_eval(M.troe + size_t(__ldg(M.troe_row + i)) * 8, a, Mc, T, mx.lnT, invT, true);
+            dlkfe = dlkf + t.D * (t.dlk0 - dlkf) + t.dlnF_dT;
+            dqdM = m * (kf * Pf - kr * Pr_) * t.D / Mc;
+        }
+        const double dlkre = dlkfe - dlKc;
+        const double Af = m * sM * kf, Ar = m * sM * kr;
+        const int nf = (s[0] < K) + (s[1] < K) + (s[2] < K), nr = (s[3] < K) + (s[4] < K) + (s[5] < K);
+        double g = Af * nf * Pf - Ar * nr * Pr_;
+        if (typ != kElem) g += dqdM * Mc;
+        const double dqdT = Af * Pf * dlkfe - Ar * Pr_ * dlkre;
+        // column derivatives for each distinct participant, scattered to its rows
+        const int16_t *pp = M.part + size_t(i) * 6;
+        const int8_t *pn = M.part_nu + size_t(i) * 6;
+        int pl[6], pnu[6];
+        double val[6];
+#pragma unroll
+        for (int t = 0; t < 6; ++t) {
+            pl[t] = __ldg(pp + t);
+            pnu[t] = __ldg(pn + t);
+            double dfl = 0.0, drl = 0.0;
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                dfl += (s[u] == pl[t]) ? d[u] : 0.0;
+                drl += (s[3 + u] == pl[t]) ? d[3 + u] : 0.0;
+            }
+            val[t] = Af * dfl - Ar * drl;
+        }
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+            if (pl[r] >= K || pnu[r] == 0) continue;
+            TJ *row = w.J + size_t(pl[r]) * P;
+#pragma unroll
+            for (int t = 0; t < 6; ++t) {
+                if (pl[t] >= K) continue;
+                atomicAdd(row + pl[t], TJ(double(pnu[r]) * val[t]));
+            }
+            if (typ != kElem) {
+                atomicAdd(w.v + pl[r], double(pnu[r]) * dqdM);
+                for (int e = __ldg(M.eff_ptr + i); e < __ldg(M.eff_ptr + i + 1); ++e)
+                    atomicAdd(row + __ldg(M.eff_sp + e), TJ(double(pnu[r]) * dqdM * __ldg(M.eff_val + e)));
+            }
+        }
+        // per-reaction Euler sum and T-derivative replace q and kf (read by this lane only)
+        w.q[i] = g;
+        w.kf[i] = dqdT;
+    }
+    __syncwarp();
+    // species sums s_k = sum_i nu_ki g_i, wT_k = sum_i nu_ki dq_i/dT
+    double sk[2] = {0.0, 0.0}, wT[2] = {0.0, 0.0}, vk[2] = {0.0, 0.0};
+    for (int h = 0; h < 2; ++h) {
+        int j = lane + 32 * h;
+        if (j < K) {
+            double a = 0.0, b = 0.0;
+            for (int e = __ldg(M.sp_ptr + j); e < __ldg(M.sp_ptr + j + 1); ++e) {
+                const double nu = double(__ldg(M.sp_nu + e));
+                const int r = __ldg(M.sp_rxn + e);
+                a += nu * w.q[r];
+                b += nu * w.kf[r];
+            }
+            sk[h] = a;
+            wT[h] = b;
+            vk[h] = w.v[j];
+        }
+    }
+    const double rho = mx.rho, Wbar = mx.Wbar, RT = kRu * T;
+    // energy row, Eq. (3): computed from the concentration Jacobian before the transform
+    double eJ[2] = {0.0, 0.0};
+    if (energy != PSR_FIXED_T) {
+        // Q = sum H_k wdot_k, S = sum H_k s_k, Hv = sum H_k v_k, dN/dT pieces
+        double Q = 0.0, Sh = 0.0, Hv = 0.0, cw = 0.0, hwT = 0.0;
+        for (int h = 0; h < 2; ++h) {
+            int j = lane + 32 * h;
+            if (j < K) {
+                const double H = w.hRT[j] * RT;
+                Q += H * wd[h];
+                Sh += H * sk[h];
+                Hv += H * vk[h];
+                cw += sl.cpR[h] * kRu * wd[h];
+                hwT += H * (wT[h] - sk[h] * invT);
+            }
+        }
+        Q = wsum(Q);
+        Sh = wsum(Sh);
+        Hv = wsum(Hv);
+        cw = wsum(cw);
+        hwT = wsum(hwT);
+        const double N = mx.N, cp = mx.cp;
+        const double inv_cpT = 1.0 / (cp * T);
+        for (int h = 0; h < 2; ++h) {
+            int j = lane + 32 * h;
+            if (j < K) {
+                double colsum = 0.0;
+                for (int k = 0; k < K; ++k) colsum += w.hRT[k] * double(w.J[size_t(k) * P + j]);
+                colsum = colsum * RT + Hv;
+                const double invWj = __ldg(M.invW + j);
+                const double dN = tau * invWj * (colsum + Wbar * (Q - Sh) / rho);
+                const double cpj = sl.cpR[h] * kRu * invWj;
+                eJ[h] = dN * inv_cpT - N * cpj * inv_cpT / cp;
+            } else if (j == K) {
+                const double dNdT = mx.sum_yin_cp + tau / rho * (cw + hwT) + tau * Q / (rho * T);
+                eJ[h] = dNdT * inv_cpT - N * mx.sum_y_dcp * inv_cpT / cp - N * inv_cpT * invT;
+            }
+        }
+    }
+    __syncwarp();
+    // species rows: dF_k/dY_j = delta_kj - tau W_k (Jc_kj + v_k)/W_j + tau W_k Wbar (s_k - wdot_k)/(rho W_j)
+    //               dF_k/dT  = -(tau W_k / rho) (wT_k + (wdot_k - s_k)/T)
+    for (int h = 0; h < 2; ++h) {
+        int k = lane + 32 * h;
+        if (k < K) {
+            const double Wk = __ldg(M.W + k);
+            const double ak = tau * Wk, bk = tau * Wk * Wbar * (sk[h] - wd[h]) / rho;
+            TJ *row = w.J + size_t(k) * P;
+            for (int j = 0; j < K; ++j) {
+                const double invWj = __ldg(M.invW + j);
+                double v = -(ak * (double(row[j]) + vk[h]) - bk) * invWj;
+                if (j == k) v += 1.0;
+                row[j] = TJ(v);
+            }
+            row[K] = TJ(-(ak / rho) * (wT[h] + (wd[h] - sk[h]) * invT));
+        }
+    }
+    __syncwarp();
+    // energy row
+    {
+        TJ *row = w.J + size_t(K) * P;
+        for (int h = 0; h < 2; ++h) {
+            int j = lane + 32 * h;
+            if (j < n) {
+                double v;
+                if (energy == PSR_FIXED_T) v = (j == K) ? 1.0 : 0.0;
+                else v = eJ[h];
+                row[j] = TJ(v);
+            }
+        }
+    }
+    __syncwarp();
+    // + diag(c)
+    for (int h = 0; h < 2; ++h) {
+        int j = lane + 32 * h;
+        if (j < n) w.J[size_t(j) * P + j] = TJ(double(w.J[size_t(j) * P + j]) + (h ? c.b : c.a));
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------- LU (partial pivoting)
+// In-place LU of w.J (n x n) with row interchanges; perm holds the final row order.
+// Returns false on a zero or non-finite pivot.
+template <class TJ>
+__device__ bool lu_factor(const WS<TJ> &w, int n) {
+    const int lane = threadIdx.x & 31;
+    const int P = w.P;
+    for (int j = lane; j < n; j += 32) w.perm[j] = int16_t(j);
+    __syncwarp();
+    for (int k = 0; k < n; ++k) {
+        // pivot: first row of largest |a_ik|, i >= k
+        double best = -1.0;
+        int bi = n;
+        for (int i = k + lane; i < n; i += 32) {
+            double a = fabs(double(w.J[size_t(i) * P + k]));
+            if (a > best || (a == best && i < bi) || a != a) {
+                if (a != a) a = INFINITY;  // a NaN pivot candidate fails the factorisation below
+                best = a;
+                bi = i;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double ob = __shfl_xor_sync(kFull, best, o);
+            int oi = __shfl_xor_sync(kFull, bi, o);
+            if (ob > best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        const int p = bi;
+        const double pv = (p < n) ? double(w.J[size_t(p) * P + k]) : 0.0;
+        if (!(pv != 0.0) || !isfinite(pv)) return false;
+        if (p != k) {
+            for (int j = lane; j < n; j += 32) {
+                TJ t = w.J[size_t(k) * P + j];
+                w.J[size_t(k) * P + j] = w.J[size_t(p) * P + j];
+                w.J[size_t(p) * P + j] = t;
+            }
+            if (lane == 0) {
+                int16_t t = w.perm[k];
+                w.perm[k] = w.perm[p];
+                w.perm[p] = t;
+            }
+        }
+        __syncwarp();
+        const TJ inv = TJ(1.0) / TJ(pv);
+        // multipliers and trailing update: lanes over rows
+        for (int i = k + 1 + lane; i < n; i += 32) {
+            TJ *ri = w.J + size_t(i) * P;
+            const TJ *rk = w.J + size_t(k) * P;
+            const TJ l = ri[k] * inv;
+            ri[k] = l;
+            for (int j = k + 1; j < n; ++j) ri[j] = fma(-l, rk[j], ri[j]);
+        }
+        __syncwarp();
+    }
+    return true;
+}
+
+// Solve (LU) x = -r with r distributed (V2), x returned as V2 (FP64 promote).
+template <class TJ>
+__device__ void lu_solve_neg(const WS<TJ> &w, int n, const V2 &r, V2 &x) {
+    const int lane = threadIdx.x & 31;
+    const int P = w.P;
+    // rhs[k] = -r[perm[k]]: stage r in rhs via the permutation
+    for (int h = 0; h < 2; ++h) {
+        int j = lane + 32 * h;
+        if (j < n) w.rhs[j] = TJ(-(h ? r.b : r.a));
+    }
+    __syncwarp();
+    TJ pr[2];
+    for (int h = 0; h < 2; ++h) {
+        int j = lane + 32 * h;
+        pr[h] = (j < n) ? w.rhs[w.perm[j]] : TJ(0);
+    }
+    __syncwarp();
+    for (int h = 0; h < 2; ++h) {
+        int j = lane + 32 * h;
+        if (j < n) w.rhs[j] = pr[h];
+    }
+    __syncwarp();
+    // forward: unit lower
+    for (int k = 0; k < n - 1; ++k) {
+        const TJ bk = w.rhs[k];
+        for (int i = k + 1 + lane; i < n; i += 32) w.rhs[i] = fma(-w.J[size_t(i) * P + k], bk, w.rhs[i]);
+        __syncwarp();
+    }
+    // backward: upper
+    for (int k = n - 1; k >= 0; --k) {
+        const TJ xk = w.rhs[k] / w.J[size_t(k) * P + k];
+        __syncwarp();
+        for (int i = lane; i < k; i += 32) w.rhs[i] = fma(-w.J[size_t(i) * P + k], xk, w.rhs[i]);
+        if (lane == 0) w.rhs[k] = xk;
+        __syncwarp();
+    }
+    x.a = (lane < n) ? double(w.rhs[lane]) : 0.0;
+    x.b = (lane + 32 < n) ? double(w.rhs[lane + 32]) : 0.0;
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------- solver pieces
+struct Reactor {
+    const double *Yin;
+    double tau, P, Tspec;
+};
+
+__device__ __forceinline__ bool all_finite(const V2 &v) {
+    return __all_sync(kFull, isfinite(v.a) && isfinite(v.b));
+}
+
+// mass fractions absolute, temperature relative
+__device__ __forceinline__ double scaled_max(const V2 &dy, const V2 &y, int K) {
+    const int lane = threadIdx.x & 31;
+    double m = 0.0;
+    for (int h = 0; h < 2; ++h) {
+        int j = lane + 32 * h;
+        if (j <= K) {
+            double d = fabs(h ? dy.b : dy.a);
+            if (j == K) d /= fabs(h ? y.b : y.a);
+            m = fmax(m, d);
+        }
+    }
+    return wmax(m);
+}
+
+__device__ __forceinline__ bool in_bounds(const V2 &y, int K, const Opts &o) {
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    for (int h = 0; h < 2; ++h) {
+        int j = lane + 32 * h;
+        double v = h ? y.b : y.a;
+        if (j < K) ok = ok && (v >= -o.y_floor);
+        else if (j == K) ok = ok && (v >= o.t_min && v <= o.t_max);
+    }
+    return __all_sync(kFull, ok);
+}
+
+__device__ __forceinline__ double max_in_bounds(const V2 &y, const V2 &dy, int K, const Opts &o) {
+    const int lane = threadIdx.x & 31;
+    double lam = INFINITY;
+    for (int h = 0; h < 2; ++h) {
+        int j = lane + 32 * h;
+        if (j > K) continue;
+        const double x = h ? y.b : y.a, d = h ? dy.b : dy.a;
+        const double lo = (j < K) ? -o.y_floor : o.t_min, hi = (j < K) ? INFINITY : o.t_max;
+        if (d < 0 && x + d < lo) lam = fmin(lam, (lo - x) / d);
+        else if (d > 0 && x + d > hi) lam = fmin(lam, (hi - x) / d);
+    }
+    return wmin(lam);
+}
+
+__device__ __forceinline__ bool step_small(const V2 &dy, const V2 &y, int K, double rtol, double atol_y,
+                                           double atol_t) {
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    for (int h = 0; h < 2; ++h) {
+        int j = lane + 32 * h;
+        if (j <= K) {
+            const double x = h ? y.b : y.a, d = h ? dy.b : dy.a;
+            ok = ok && (fabs(d) <= rtol * fabs(x) + ((j < K) ? atol_y : atol_t));
+        }
+    }
+    return __all_sync(kFull, ok);
+}
+
+__device__ __forceinline__ V2 axpy(const V2 &x, double a, const V2 &d) { return V2{x.a + a * d.a, x.b + a * d.b}; }
+
+struct Ctx {
+    DevMech M;
+    Opts o;
+    Reactor r;
+    const double *mult;
+    int nfev;
+    Mix mx;
+    SpecLane sl;
+    int K, n;
+};
+
+template <class TJ>
+__device__ void residual_R(Ctx &cx, const WS<TJ> &w, const V2 &y, const V2 &c, const V2 &xref, V2 &F, V2 &R) {
+    ++cx.nfev;
+    eval_F(cx.M, w, y, F, cx.mx, cx.sl, cx.r.Yin, cx.r.tau, cx.r.P, cx.r.Tspec, cx.o.energy, cx.mult);
+    R.a = F.a + c.a * (y.a - xref.a);
+    R.b = F.b + c.b * (y.b - xref.b);
+}
+
+// Damped Newton on R(y) = F(y) + c (y - xref) from y (see the oracle's description).
+template <class TJ>
+__device__ bool damped_newton(Ctx &cx, const WS<TJ> &w, V2 &y, const V2 &xref, const V2 &c, int max_it,
+                              bool steady, int &counter) {
+    const int K = cx.K, n = cx.n;
+    const Opts &o = cx.o;
+    V2 F, R;
+    residual_R(cx, w, y, c, xref, F, R);
+    double dn_prev = INFINITY;
+    for (int it = 0; it < max_it; ++it) {
+        if (counter >= o.max_newton) break;
+        ++counter;
+        eval_J(cx.M, w, y, c, cx.mx, cx.sl, cx.r.Yin, cx.r.tau, o.energy, cx.mult);
+        if (!lu_factor(w, n)) break;
+        V2 dy;
+        lu_solve_neg(w, n, R, dy);
+        if (!all_finite(dy)) break;
+        if (steady) {
+            const double rmax = wmax(fmax(fabs(R.a), fabs(R.b)));
+            if (rmax <= o.ftol && step_small(dy, y, K, o.step_rtol, o.step_atol_y, o.step_atol_t)) {
+                y = axpy(y, 1.0, dy);
+                return true;
+            }
+        } else if (step_small(dy, y, K, o.ts_rtol, o.ts_atol_y, o.ts_rtol)) {
+            y = axpy(y, 1.0, dy);
+            return true;
+        }
+        const double dn = scaled_max(dy, y, K);
+        if (dn >= dn_prev) break;
+        dn_prev = dn;
+        double lam = fmin(1.0, max_in_bounds(y, dy, K, o));
+        bool accepted = false;
+        V2 yt, Rt;
+        for (int d = 0; d < o.max_damp; ++d) {
+            yt = axpy(y, lam, dy);
+            if (in_bounds(yt, K, o)) {
+                V2 Ft;
+                residual_R(cx, w, yt, c, xref, Ft, Rt);
+                if (all_finite(Rt)) {
+                    V2 db;
+                    lu_solve_neg(w, n, Rt, db);
+                    if (scaled_max(db, y, K) < dn) {
+                        accepted = true;
+                        break;
+                    }
+                }
+            }
+            lam *= 0.5;
+        }
+        if (!accepted) break;
+        y = yt;
+        R = Rt;
+    }
+    return false;
+}
+
+template <class TJ>
+__device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) {
+    const int lane = threadIdx.x & 31;
+    const int K = cx.K;
+    const Opts &o = cx.o;
+    const double tau = bt.tau[r];
+    cx.r.Yin = bt.Y_in + r * K;
+    cx.r.tau = tau;
+    cx.r.P = bt.P[r];
+    cx.r.Tspec = bt.T0[r];
+    cx.nfev = 0;
+    // inlet enthalpy sum_k Y_k,in h_k(T_in)
+    {
+        const double Tin = bt.T_in[r], lnTin = log(Tin);
+        double s = 0.0;
+        for (int h = 0; h < 2; ++h) {
+            int j = lane + 32 * h;
+            if (j < K) {
+                double cpR, hRT, sR, dcpR;
+                nasa7(cx.M.nasa, j, Tin, lnTin, cpR, hRT, sR, dcpR);
+                s += cx.r.Yin[j] * hRT * __ldg(cx.M.invW + j);
+            }
+        }
+        cx.mx.h_in = wsum(s) * kRu * Tin;
+    }
+    V2 x;
+    x.a = (lane < K) ? bt.Y0[r * K + lane] : (lane == K ? bt.T0[r] : 0.0);
+    x.b = (lane + 32 < K) ? bt.Y0[r * K + lane + 32] : (lane + 32 == K ? bt.T0[r] : 0.0);
+    const V2 zero{0.0, 0.0};
+    V2 F, R;
+    residual_R(cx, w, x, zero, x, F, R);
+    int status, counter = 0, ts = 0, rounds = 0;
+    V2 out = x;
+    if (!all_finite(F)) {
+        status = PSR_NONFINITE;
+    } else {
+        double dt = o.dt0_over_tau * tau;
+        while (true) {
+            V2 y = x;
+            bool conv = damped_newton(cx, w, y, x, zero, o.max_newton, true, counter);
+            if (conv) {
+                status = PSR_CONVERGED;
+                out = y;
+                break;
+            }
+            if (counter >= o.max_newton) {
+                status = PSR_MAX_ITER;
+                out = y;
+                break;
+            }
+            ++rounds;
+            if (rounds > o.max_ts_rounds) {
+                status = PSR_TS_EXHAUSTED;
+                out = x;
+                break;
+            }
+            int taken = 0;
+            bool done = false;
+            while (taken < o.ts_steps) {
+                const double Tx = comp_get(x, K);
+                const double s = tau / dt;
+                V2 c;
+                c.a = (lane < K) ? s : (lane == K ? (o.energy == PSR_FIXED_T ? s : s / Tx) : 0.0);
+                c.b = (lane + 32 < K) ? s : (lane + 32 == K ? (o.energy == PSR_FIXED_T ? s : s / Tx) : 0.0);
+                const int used0 = counter;
+                V2 y = x;
+                bool ok = damped_newton(cx, w, y, x, c, o.ts_newton, false, counter);
+                const int used = counter - used0;
+                if (counter >= o.max_newton) {
+                    status = PSR_MAX_ITER;
+                    out = x;
+                    done = true;
+                    break;
+                }
+                if (ok) {
+                    x = y;
+                    ++taken;
+                    ++ts;
+                    const double g = (used <= 3) ? 2.0 : (used == 4 ? 1.25 : 1.0);
+                    dt = fmin(g * dt, 1e6 * tau);
+                } else {
+                    dt *= o.dt_shrink;
+                    if (dt < 1e-16 * tau) {
+                        status = PSR_TS_EXHAUSTED;
+                        out = x;
+                        done = true;
+                        break;
+                    }
+                }
+            }
+            if (done) break;
+        }
+    }
+    // report ||F||_inf at the output state
+    residual_R(cx, w, out, zero, out, F, R);
+    const double fn = wmax(fmax(fabs(F.a), fabs(F.b)));
+    if (lane < K) bt.Y_out[r * K + lane] = out.a;
+    if (lane + 32 < K) bt.Y_out[r * K + lane + 32] = out.b;
+    const double Tout = comp_get(out, K);
+    if (lane == 0) {
+        bt.T_out[r] = Tout;
+        if (bt.status) bt.status[r] = status;
+        if (bt.iters) bt.iters[r] = counter;
+        if (bt.ts_steps) bt.ts_steps[r] = ts;
+        if (bt.fnorm) bt.fnorm[r] = fn;
+        if (bt.nfev) bt.nfev[r] = cx.nfev;
+    }
+}
+
+template <class TJ>
+__global__ void solve_kernel(DevMech M, Batch bt, Opts o, int *queue, size_t ws_per_warp) {
+    extern __shared__ __align__(16) char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WS<TJ> w = carve<TJ>(smem + warp * ws_per_warp, M.K, M.I, M.K + 1);
+    Ctx cx;
+    cx.M = M;
+    cx.o = o;
+    cx.mult = bt.rate_mult;
+    cx.K = M.K;
+    cx.n = M.K + 1;
+    while (true) {
+        int r = 0;
+        if (lane == 0) r = atomicAdd(queue, 1);
+        r = __shfl_sync(kFull, r, 0);
+        if (r >= bt.B) break;
+        solve_one<TJ>(cx, w, bt, r);
+    }
+}
+
+// residual / Jacobian at given states: one warp per state
+template <class TJ>
+__global__ void eval_kernel(DevMech M, Batch bt, int energy, int want_J, double *out, size_t ws_per_warp) {
+    extern __shared__ __align__(16) char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r = int64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
+    if (r >= bt.B) return;
+    WS<TJ> w = carve<TJ>(smem + warp * ws_per_warp, M.K, M.I, M.K + 1);
+    Ctx cx;
+    cx.M = M;
+    cx.mult = bt.rate_mult;
+    cx.K = M.K;
+    cx.n = M.K + 1;
+    cx.o.energy = energy;
+    const int K = M.K, n = K + 1;
+    cx.r.Yin = bt.Y_in + r * K;
+    cx.r.tau = bt.tau[r];
+    cx.r.P = bt.P[r];
+    cx.r.Tspec = bt.T0[r];
+    {
+        const double Tin = bt.T_in[r], lnTin = log(Tin);
+        double s = 0.0;
+        for (int h = 0; h < 2; ++h) {
+            int j = lane + 32 * h;
+            if (j < K) {
+                double cpR, hRT, sR, dcpR;
+                nasa7(M.nasa, j, Tin, lnTin, cpR, hRT, sR, dcpR);
+                s += cx.r.Yin[j] * hRT * __ldg(M.invW + j);
+            }
+        }
+        cx.mx.h_in = wsum(s) * kRu * Tin;
+    }
+    V2 y;
+    y.a = (lane < K) ? bt.Y0[r * K + lane] : (lane == K ? bt.T0[r] : 0.0);
+    y.b = (lane + 32 < K) ? bt.Y0[r * K + lane + 32] : (lane + 32 == K ? bt.T0[r] : 0.0);
+    const V2 zero{0.0, 0.0};
+    V2 F, R;
+    residual_R(cx, w, y, zero, y, F, R);
+    if (!want_J) {
+        if (lane < n) out[r * n + lane] = F.a;
+        if (lane + 32 < n) out[r * n + lane + 32] = F.b;
+        return;
+    }
+    eval_J(M, w, y, zero, cx.mx, cx.sl, cx.r.Yin, cx.r.tau, energy, cx.mult);
+    for (int idx = lane; idx < n * n; idx += 32)
+        out[r * n * n + idx] = double(w.J[size_t(idx / n) * w.P + idx % n]);
+}
+
+template <class TJ>
+__global__ void lu_kernel(int64_t B, int n, const double *A, const double *rhs, double *x, int32_t *ok,
+                          size_t ws_per_warp) {
+    extern __shared__ __align__(16) char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t b = int64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
+    if (b >= B) return;
+    WS<TJ> w = carve<TJ>(smem + warp * ws_per_warp, 0, 0, n);
+    for (int idx = lane; idx < n * n; idx += 32) w.J[size_t(idx / n) * w.P + idx % n] = TJ(A[b * n * n + idx]);
+    __syncwarp();
+    V2 r;
+    r.a = (lane < n) ? rhs[b * n + lane] : 0.0;
+    r.b = (lane + 32 < n) ? rhs[b * n + lane + 32] : 0.0;
+    bool good = lu_factor(w, n);
+    V2 xs{0.0, 0.0};
+    if (good) {
+        V2 nr{-r.a, -r.b};
+        lu_solve_neg(w, n, nr, xs);
+    }
+    if (lane < n) x[b * n + lane] = xs.a;
+    if (lane + 32 < n) x[b * n + lane + 32] = xs.b;
+    if (lane == 0) ok[b] = good ? 1 : 0;
+}
+
+// ---------------------------------------------------------------- host side
+Opts to_opts(const psr_options *po) {
+    psr_options d;
+    psr_options_default(&d);
+    const psr_options &s = po ? *po : d;
+    Opts o;
+    o.ftol = s.ftol;
+    o.step_rtol = s.step_rtol;
+    o.step_atol_y = s.step_atol_y;
+    o.step_atol_t = s.step_atol_t;
+    o.ts_rtol = s.ts_rtol;
+    o.ts_atol_y = s.ts_atol_y;
+    o.dt0_over_tau = s.dt0_over_tau;
+    o.dt_shrink = s.dt_shrink;
+    o.y_floor = s.y_floor;
+    o.t_min = s.t_min;
+    o.t_max = s.t_max;
+    o.max_newton = s.max_newton;
+    o.max_damp = s.max_damp;
+    o.max_ts_rounds = s.max_ts_rounds;
+    o.ts_steps = s.ts_steps;
+    o.ts_newton = s.ts_newton;
+    o.energy = s.energy;
+    return o;
+}
+
+int check_opts(const psr_options *po) {
+    if (!po) return PSR_OK;
+    const psr_options &s = *po;
+    if (!(s.ftol > 0) || !(s.step_rtol >= 0) || !(s.step_atol_y >= 0) || !(s.step_atol_t >= 0) ||
+        !(s.ts_rtol > 0) || !(s.ts_atol_y >= 0) || !(s.dt0_over_tau > 0) || !(s.dt_shrink > 0 && s.dt_shrink < 1) ||
+        !(s.y_floor >= 0) || !(s.t_min > 0 && s.t_max > s.t_min) || s.max_newton < 1 || s.max_damp < 1 ||
+        s.max_ts_rounds < 0 || s.ts_steps < 1 || s.ts_newton < 1 ||
+        (s.precision != PSR_FP64 && s.precision != PSR_MIXED) ||
+        (s.energy != PSR_ADIABATIC && s.energy != PSR_FIXED_T) || s.warps_per_block < 0 || s.warps_per_block > 32 ||
+        s.blocks_per_sm < 0)
+        return set_error(PSR_E_ARG, "psr_options: value out of range");
+    return PSR_OK;
+}
+
+template <class TJ>
+int launch_solve(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int bps_req, cudaStream_t st) {
+    const size_t wsb = ws_bytes<TJ>(m.K, m.I, m.K + 1);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int max_smem = 0, nsm = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int wpb = wpb_req > 0 ? wpb_req : 4;
+    while (wpb > 1 && size_t(wpb) * wsb > size_t(max_smem)) --wpb;
+    const size_t smem = size_t(wpb) * wsb;
+    if (smem > size_t(max_smem))
+        return set_error(PSR_E_UNSUPPORTED, "mechanism too large for one warp's shared memory");
+    cudaError_t e = cudaFuncSetAttribute(solve_kernel<TJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return cuda_error("cudaFuncSetAttribute", e);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel<TJ>, wpb * 32, smem);
+    if (e != cudaSuccess) return cuda_error("occupancy", e);
+    if (per_sm < 1) return set_error(PSR_E_UNSUPPORTED, "solver kernel does not fit on an SM");
+    if (bps_req > 0 && bps_req < per_sm) per_sm = bps_req;
+    int64_t want = (bt.B + wpb - 1) / wpb;
+    int64_t grid = std::min<int64_t>(int64_t(per_sm) * nsm, want);
+    if (grid < 1) grid = 1;
+    int *queue = nullptr;
+    e = cudaMallocAsync(reinterpret_cast<void **>(&queue), sizeof(int), st);
+    if (e != cudaSuccess) return set_error(PSR_E_OOM, "work-queue allocation failed");
+    cudaMemsetAsync(queue, 0, sizeof(int), st);
+    DevMech D = m.dev;
+    solve_kernel<TJ><<<unsigned(grid), wpb * 32, smem, st>>>(D, bt, o, queue, wsb);
+    e = cudaGetLastError();
+    cudaFreeAsync(queue, st);
+    if (e != cudaSuccess) return cuda_error("solve_kernel launch", e);
+    return PSR_OK;
+}
+
+template <class TJ>
+int launch_eval(const Mech &m, const Batch &bt, int energy, int want_J, double *out, cudaStream_t st) {
+    const size_t wsb = ws_bytes<TJ>(m.K, m.I, m.K + 1);
+    const int wpb = 2;
+    const size_t smem = wpb * wsb;
+    cudaError_t e = cudaFuncSetAttribute(eval_kernel<TJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return cuda_error("cudaFuncSetAttribute", e);
+    const int64_t grid = (bt.B + wpb - 1) / wpb;
+    eval_kernel<TJ><<<unsigned(grid), wpb * 32, smem, st>>>(m.dev, bt, energy, want_J, out, wsb);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error("eval_kernel launch", e);
+    return PSR_OK;
+}
+
+int check_mech(const psr_mech *m) {
+    if (!m) return set_error(PSR_E_ARG, "mechanism is NULL");
+    if (m->m.K + 1 > kMaxWarpN)
+        return set_error(PSR_E_UNSUPPORTED, "this kernel handles K + 1 <= 64 species unknowns");
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != m->m.device) return set_error(PSR_E_ARG, "mechanism was loaded on another CUDA device");
+    return PSR_OK;
+}
+
+}  // namespace
+}  // namespace psr
+
+using namespace psr;
+
+extern "C" {
+
+int psr_batch_solve(const psr_mech *m, int64_t B, const double *Y_in, const double *T_in, const double *tau,
+                    const double *P, const double *Y0, const double *T0, const double *rate_mult, double *Y_out,
+                    double *T_out, int32_t *iters, int32_t *ts_steps, int32_t *status, double *fnorm,
+                    int32_t *nfev, const psr_options *opt, void *cuda_stream) {
+    int rc = check_mech(m);
+    if (rc) return rc;
+    if (B < 0) return set_error(PSR_E_ARG, "B < 0");
+    if (B == 0) return PSR_OK;
+    if (B > (int64_t(1) << 31) - 64) return set_error(PSR_E_ARG, "B too large");
+    if (!Y_in || !T_in || !tau || !P || !Y0 || !T0 || !Y_out || !T_out)
+        return set_error(PSR_E_ARG, "psr_batch_solve: required pointer is NULL");
+    if ((rc = check_opts(opt))) return rc;
+    Batch bt{B, Y_in, T_in, tau, P, Y0, T0, rate_mult, Y_out, T_out, fnorm, iters, ts_steps, status, nfev};
+    const Opts o = to_opts(opt);
+    psr_options d;
+    psr_options_default(&d);
+    const psr_options &po = opt ? *opt : d;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (po.precision == PSR_MIXED) return launch_solve<float>(m->m, bt, o, po.warps_per_block, po.blocks_per_sm, st);
+    return launch_solve<double>(m->m, bt, o, po.warps_per_block, po.blocks_per_sm, st);
+}
+
+int psr_batch_solve_host(const psr_mech *m, int64_t B, const double *Y_in, const double *T_in, const double *tau,
+                         const double *P, const double *Y0, const double *T0, const double *rate_mult,
+                         double *Y_out, double *T_out, int32_t *iters, int32_t *ts_steps, int32_t *status,
+                         double *fnorm, int32_t *nfev, const psr_options *opt, void *cuda_stream) {
+    int rc = check_mech(m);
+    if (rc) return rc;
+    if (B < 0) return set_error(PSR_E_ARG, "B < 0");
+    if (B == 0) return PSR_OK;
+    if (!Y_in || !T_in || !tau || !P || !Y0 || !T0 || !Y_out || !T_out)
+        return set_error(PSR_E_ARG, "psr_batch_solve_host: required pointer is NULL");
+    const int K = m->m.K, I = m->m.I;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const size_t nb = size_t(B);
+    // one device buffer: inputs, outputs
+    const size_t doubles = nb * K * 3 + nb * 6 + (rate_mult ? I : 0);
+    const size_t ints = nb * 4;
+    char *buf = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&buf), doubles * 8 + ints * 4 + 64, st);
+    if (e != cudaSuccess) return set_error(PSR_E_OOM, "device buffers for psr_batch_solve_host");
+    double *d = reinterpret_cast<double *>(buf);
+    double *dYin = d, *dY0 = d + nb * K, *dYout = d + 2 * nb * K;
+    double *dTin = d + 3 * nb * K, *dtau = dTin + nb, *dP = dtau + nb, *dT0 = dP + nb, *dTout = dT0 + nb,
+           *dfn = dTout + nb;
+    double *dmult = rate_mult ? dfn + nb : nullptr;
+    int32_t *ip = reinterpret_cast<int32_t *>(buf + doubles * 8);
+    int32_t *dit = ip, *dts = ip + nb, *dst = ip + 2 * nb, *dnf = ip + 3 * nb;
+    cudaMemcpyAsync(dYin, Y_in, nb * K * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(dY0, Y0, nb * K * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(dTin, T_in, nb * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(dtau, tau, nb * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(dP, P, nb * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(dT0, T0, nb * 8, cudaMemcpyHostToDevice, st);
+    if (rate_mult) cudaMemcpyAsync(dmult, rate_mult, size_t(I) * 8, cudaMemcpyHostToDevice, st);
+    rc = psr_batch_solve(m, B, dYin, dTin, dtau, dP, dY0, dT0, dmult, dYout, dTout, dit, dts, dst, dfn, dnf, opt,
+                         st);
+    if (rc == PSR_OK) {
+        cudaMemcpyAsync(Y_out, dYout, nb * K * 8, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(T_out, dTout, nb * 8, cudaMemcpyDeviceToHost, st);
+        if (fnorm) cudaMemcpyAsync(fnorm, dfn, nb * 8, cudaMemcpyDeviceToHost, st);
+        if (iters) cudaMemcpyAsync(iters, dit, nb * 4, cudaMemcpyDeviceToHost, st);
+        if (ts_steps) cudaMemcpyAsync(ts_steps, dts, nb * 4, cudaMemcpyDeviceToHost, st);
+        if (status) cudaMemcpyAsync(status, dst, nb * 4, cudaMemcpyDeviceToHost, st);
+        if (nfev) cudaMemcpyAsync(nfev, dnf, nb * 4, cudaMemcpyDeviceToHost, st);
+    }
+    cudaFreeAsync(buf, st);
+    e = cudaStreamSynchronize(st);
+    if (rc == PSR_OK && e != cudaSuccess) return cuda_error("psr_batch_solve_host", e);
+    return rc;
+}
+
+int psr_eval_residual(const psr_mech *m, int64_t B, const double *Y_in, const double *T_in, const double *tau,
+                      const double *P, const double *Y, const double *T, const double *rate_mult, double *F_out,
+                      int32_t energy, void *cuda_stream) {
+    int rc = check_mech(m);
+    if (rc) return rc;
+    if (B < 0 || (energy != PSR_ADIABATIC && energy != PSR_FIXED_T)) return set_error(PSR_E_ARG, "bad B or energy");
+    if (B == 0) return PSR_OK;
+    if (!Y_in || !T_in || !tau || !P || !Y || !T || !F_out) return set_error(PSR_E_ARG, "NULL pointer");
+    Batch bt{B, Y_in, T_in, tau, P, Y, T, rate_mult, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    return launch_eval<double>(m->m, bt, energy, 0, F_out, static_cast<cudaStream_t>(cuda_stream));
+}
+
+int psr_eval_jacobian(const psr_mech *m, int64_t B, const double *Y_in, const double *T_in, const double *tau,
+                      const double *P, const double *Y, const double *T, const double *rate_mult, double *J_out,
+                      int32_t energy, int32_t precision, void *cuda_stream) {
+    int rc = check_mech(m);
+    if (rc) return rc;
+    if (B < 0 || (energy != PSR_ADIABATIC && energy != PSR_FIXED_T) ||
+        (precision != PSR_FP64 && precision != PSR_MIXED))
+        return set_error(PSR_E_ARG, "bad B, energy or precision");
+    if (B == 0) return PSR_OK;
+    if (!Y_in || !T_in || !tau || !P || !Y || !T || !J_out) return set_error(PSR_E_ARG, "NULL pointer");
+    Batch bt{B, Y_in, T_in, tau, P, Y, T, rate_mult, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (precision == PSR_MIXED) return launch_eval<float>(m->m, bt, energy, 1, J_out, st);
+    return launch_eval<double>(m->m, bt, energy, 1, J_out, st);
+}
+
+int psr_batch_lu_solve(int64_t B, int32_t n, const double *A, const double *r, double *x_out, int32_t *ok_out,
+                       int32_t precision, void *cuda_stream) {
+    if (B < 0 || n < 1 || n > kMaxWarpN || (precision != PSR_FP64 && precision != PSR_MIXED))
+        return set_error(PSR_E_ARG, "psr_batch_lu_solve: bad B, n or precision");
+    if (B == 0) return PSR_OK;
+    if (!A || !r || !x_out || !ok_out) return set_error(PSR_E_ARG, "psr_batch_lu_solve: NULL pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int wpb = 4;
+    const int64_t grid = (B + wpb - 1) / wpb;
+    cudaError_t e;
+    if (precision == PSR_MIXED) {
+        const size_t wsb = ws_bytes<float>(0, 0, n);
+        e = cudaFuncSetAttribute(lu_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(wpb * wsb));
+        if (e != cudaSuccess) return cuda_error("cudaFuncSetAttribute", e);
+        lu_kernel<float><<<unsigned(grid), wpb * 32, wpb * wsb, st>>>(B, n, A, r, x_out, ok_out, wsb);
+    } else {
+        const size_t wsb = ws_bytes<double>(0, 0, n);
+        e = cudaFuncSetAttribute(lu_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(wpb * wsb));
+        if (e != cudaSuccess) return cuda_error("cudaFuncSetAttribute", e);
+        lu_kernel<double><<<unsigned(grid), wpb * 32, wpb * wsb, st>>>(B, n, A, r, x_out, ok_out, wsb);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error("lu_kernel launch", e);
+    return PSR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,259 @@
+"""ctypes binding of libpsr (include/psr.h): argument marshalling only.
+
+Every computation runs in the CUDA library; there is no CPU fallback. Device arrays
+are torch CUDA tensors (float64 / int32, contiguous), passed by pointer with the
+current torch stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpsr.so")
+
+PSR_OK = 0
+PSR_CONVERGED, PSR_MAX_ITER, PSR_NONFINITE, PSR_TS_EXHAUSTED = 0, 1, 2, 4
+PSR_FP64, PSR_MIXED = 0, 1
+PSR_ADIABATIC, PSR_FIXED_T = 0, 1
+
+
+class PsrError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libpsr error {code}: {msg}")
+        self.code = code
+
+
+class CMechInfo(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("I", ctypes.c_int32), ("n_elements", ctypes.c_int32),
+                ("n_third_body", ctypes.c_int32), ("n_falloff", ctypes.c_int32),
+                ("has_soot", ctypes.c_int32)]
+
+
+class COptions(ctypes.Structure):
+    _fields_ = [("ftol", ctypes.c_double), ("step_rtol", ctypes.c_double),
+                ("step_atol_y", ctypes.c_double), ("step_atol_t", ctypes.c_double),
+                ("ts_rtol", ctypes.c_double), ("ts_atol_y", ctypes.c_double),
+                ("dt0_over_tau", ctypes.c_double), ("dt_shrink", ctypes.c_double),
+                ("y_floor", ctypes.c_double), ("t_min", ctypes.c_double), ("t_max", ctypes.c_double),
+                ("max_newton", ctypes.c_int32), ("max_damp", ctypes.c_int32),
+                ("max_ts_rounds", ctypes.c_int32), ("ts_steps", ctypes.c_int32),
+                ("ts_newton", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("energy", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libpsr; raises if it was not built (run __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p
+        L.psr_mech_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(vp)]
+        L.psr_mech_load_mem.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(vp)]
+        L.psr_mech_info_get.argtypes = [vp, ctypes.POINTER(CMechInfo)]
+        L.psr_mech_weights.argtypes = [vp, dp]
+        L.psr_mech_free.argtypes = [vp]
+        L.psr_mech_free.restype = None
+        L.psr_options_default.argtypes = [ctypes.POINTER(COptions)]
+        L.psr_options_default.restype = None
+        L.psr_last_error.restype = ctypes.c_char_p
+        solve_args = [vp, i64] + [dp] * 7 + [dp] * 2 + [dp] * 5 + [ctypes.POINTER(COptions), vp]
+        L.psr_batch_solve.argtypes = solve_args
+        L.psr_batch_solve_host.argtypes = solve_args
+        L.psr_eval_residual.argtypes = [vp, i64] + [dp] * 7 + [dp, i32, vp]
+        L.psr_eval_jacobian.argtypes = [vp, i64] + [dp] * 7 + [dp, i32, i32, vp]
+        L.psr_batch_lu_solve.argtypes = [i64, i32, dp, dp, dp, dp, i32, vp]
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != PSR_OK:
+        raise PsrError(rc, lib().psr_last_error().decode())
+
+
+@dataclasses.dataclass
+class Options:
+    """Solver controls, field for field as psr_options (defaults from the library)."""
+    ftol: float = 1e-8
+    step_rtol: float = 1e-10
+    step_atol_y: float = 1e-14
+    step_atol_t: float = 1e-10
+    ts_rtol: float = 1e-4
+    ts_atol_y: float = 1e-10
+    dt0_over_tau: float = 1e-10
+    dt_shrink: float = 0.25
+    y_floor: float = 1e-10
+    t_min: float = 200.0
+    t_max: float = 5000.0
+    max_newton: int = 500
+    max_damp: int = 8
+    max_ts_rounds: int = 100
+    ts_steps: int = 12
+    ts_newton: int = 8
+    precision: int = PSR_FP64
+    energy: int = PSR_ADIABATIC
+    warps_per_block: int = 0
+    blocks_per_sm: int = 0
+
+    def to_c(self):
+        o = COptions()
+        lib().psr_options_default(ctypes.byref(o))
+        for f in dataclasses.fields(self):
+            setattr(o, f.name, getattr(self, f.name))
+        return o
+
+
+class Mechanism:
+    """A mechanism loaded into libpsr (tables on the current CUDA device)."""
+
+    def __init__(self, text: str):
+        h = ctypes.c_void_p()
+        raw = text.encode()
+        _check(lib().psr_mech_load_mem(raw, len(raw), ctypes.byref(h)))
+        self._h = h
+        info = CMechInfo()
+        _check(lib().psr_mech_info_get(h, ctypes.byref(info)))
+        self.K, self.I = info.K, info.I
+        self.n_third_body, self.n_falloff, self.has_soot = info.n_third_body, info.n_falloff, bool(info.has_soot)
+        W = np.zeros(self.K)
+        _check(lib().psr_mech_weights(h, W.ctypes.data))
+        self.W = W
+
+    @classmethod
+    def from_file(cls, path):
+        with open(path) as fh:
+            return cls(fh.read())
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().psr_mech_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ptr(t, dtype, shape=None, name="array"):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.data_ptr()
+
+
+def _stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def batch_solve(mech: Mechanism, Y_in, T_in, tau, P, Y0, T0, rate_mult=None, opts: Options = None,
+                out=None):
+    """psr_batch_solve on torch CUDA tensors. Returns dict Y, T, iters, ts_steps, status, fnorm, nfev."""
+    import torch
+    f64, i32 = torch.float64, torch.int32
+    B, K = Y_in.shape
+    dev = Y_in.device
+    if out is None:
+        out = dict(Y=torch.empty((B, K), dtype=f64, device=dev), T=torch.empty(B, dtype=f64, device=dev),
+                   iters=torch.empty(B, dtype=i32, device=dev), ts_steps=torch.empty(B, dtype=i32, device=dev),
+                   status=torch.empty(B, dtype=i32, device=dev), fnorm=torch.empty(B, dtype=f64, device=dev),
+                   nfev=torch.empty(B, dtype=i32, device=dev))
+    o = (opts or Options()).to_c()
+    _check(lib().psr_batch_solve(
+        mech.handle, B, _ptr(Y_in, f64, (B, K), "Y_in"), _ptr(T_in, f64, (B,), "T_in"),
+        _ptr(tau, f64, (B,), "tau"), _ptr(P, f64, (B,), "P"), _ptr(Y0, f64, (B, K), "Y0"),
+        _ptr(T0, f64, (B,), "T0"), _ptr(rate_mult, f64, (mech.I,), "rate_mult"),
+        _ptr(out["Y"], f64, (B, K)), _ptr(out["T"], f64, (B,)), _ptr(out["iters"], i32, (B,)),
+        _ptr(out["ts_steps"], i32, (B,)), _ptr(out["status"], i32, (B,)), _ptr(out["fnorm"], f64, (B,)),
+        _ptr(out["nfev"], i32, (B,)), ctypes.byref(o), _stream()))
+    return out
+
+
+def batch_solve_host(mech: Mechanism, Y_in, T_in, tau, P, Y0, T0, rate_mult=None, opts: Options = None,
+                     out=None, stream=None):
+    """psr_batch_solve_host on host arrays (numpy float64, or CPU torch tensors, pinned
+    for the fast path): the library copies inputs in, solves, copies results back and
+    synchronises. Returns dict Y, T, iters, ts_steps, status, fnorm, nfev (host)."""
+    def addr(x, dtype):
+        if hasattr(x, "data_ptr"):
+            import torch
+            want = torch.float64 if dtype == np.float64 else torch.int32
+            if x.is_cuda or x.dtype != want or not x.is_contiguous():
+                raise TypeError("host arrays must be contiguous CPU tensors of the right dtype")
+            return x.data_ptr()
+        if x.dtype != dtype or not x.flags["C_CONTIGUOUS"]:
+            raise TypeError("host arrays must be contiguous numpy arrays of the right dtype")
+        return x.ctypes.data
+    B, K = Y_in.shape
+    if out is None:
+        out = dict(Y=np.empty((B, K)), T=np.empty(B), iters=np.empty(B, np.int32),
+                   ts_steps=np.empty(B, np.int32), status=np.empty(B, np.int32), fnorm=np.empty(B),
+                   nfev=np.empty(B, np.int32))
+    ins = [v if hasattr(v, "data_ptr") else np.ascontiguousarray(v, dtype=np.float64)
+           for v in (Y_in, T_in, tau, P, Y0, T0)]
+    mult = None if rate_mult is None else np.ascontiguousarray(rate_mult, dtype=np.float64)
+    o = (opts or Options()).to_c()
+    _check(lib().psr_batch_solve_host(
+        mech.handle, B, *[addr(v, np.float64) for v in ins], None if mult is None else mult.ctypes.data,
+        addr(out["Y"], np.float64), addr(out["T"], np.float64), addr(out["iters"], np.int32),
+        addr(out["ts_steps"], np.int32), addr(out["status"], np.int32), addr(out["fnorm"], np.float64),
+        addr(out["nfev"], np.int32), ctypes.byref(o), stream if stream is not None else _stream()))
+    return out
+
+
+def eval_residual(mech: Mechanism, Y_in, T_in, tau, P, Y, T, rate_mult=None, energy=PSR_ADIABATIC):
+    import torch
+    f64 = torch.float64
+    B, K = Y.shape
+    F = torch.empty((B, K + 1), dtype=f64, device=Y.device)
+    _check(lib().psr_eval_residual(
+        mech.handle, B, _ptr(Y_in, f64, (B, K)), _ptr(T_in, f64, (B,)), _ptr(tau, f64, (B,)),
+        _ptr(P, f64, (B,)), _ptr(Y, f64, (B, K)), _ptr(T, f64, (B,)), _ptr(rate_mult, f64, (mech.I,)),
+        F.data_ptr(), energy, _stream()))
+    return F
+
+
+def eval_jacobian(mech: Mechanism, Y_in, T_in, tau, P, Y, T, rate_mult=None, energy=PSR_ADIABATIC,
+                  precision=PSR_FP64):
+    import torch
+    f64 = torch.float64
+    B, K = Y.shape
+    J = torch.empty((B, K + 1, K + 1), dtype=f64, device=Y.device)
+    _check(lib().psr_eval_jacobian(
+        mech.handle, B, _ptr(Y_in, f64, (B, K)), _ptr(T_in, f64, (B,)), _ptr(tau, f64, (B,)),
+        _ptr(P, f64, (B,)), _ptr(Y, f64, (B, K)), _ptr(T, f64, (B,)), _ptr(rate_mult, f64, (mech.I,)),
+        J.data_ptr(), energy, precision, _stream()))
+    return J
+
+
+def batch_lu_solve(A, r, precision=PSR_FP64):
+    """Solve A_b x_b = r_b for a batch of n x n systems (n <= 64) by the solver's LU."""
+    import torch
+    B, n, _ = A.shape
+    x = torch.empty((B, n), dtype=torch.float64, device=A.device)
+    ok = torch.empty(B, dtype=torch.int32, device=A.device)
+    _check(lib().psr_batch_lu_solve(B, n, _ptr(A, torch.float64, (B, n, n), "A"), _ptr(r, torch.float64, (B, n), "r"),
+                                    x.data_ptr(), ok.data_ptr(), precision, _stream()))
+    return x, ok

@@ -1,0 +1,275 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element by element,
+on seeded inputs (residual, Jacobian, LU, full solves), plus edge cases and properties
+that hold at any size (element conservation, residual norm) for the full batches."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import psr_oracle as O
+from paper_2005_11468_gb300 import psr, synth
+from tests.oracle_helpers import golden_text, random_states, workload
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+
+Y_REL, Y_MIN, T_ABS = 1e-6, 1e-10, 1e-8        # parity bar: Y_k > 1e-10 to 1e-6 relative, T to 1e-8 K
+
+
+@pytest.fixture(scope="module")
+def dev():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_11468_gb300 import _build
+    _build.build()
+    return torch.device("cuda:0")
+
+
+_MECH = {}
+
+
+def gpu_mech(name):
+    if name not in _MECH:
+        spec, _, _ = workload(name)
+        _MECH[name] = psr.Mechanism(synth.mechanism_text(spec))
+    return _MECH[name]
+
+
+def to_dev(batch, dev):
+    import torch
+    return {k: torch.tensor(np.ascontiguousarray(getattr(batch, k)), dtype=torch.float64, device=dev)
+            for k in ("Y_in", "T_in", "tau", "P", "Y0", "T0")}
+
+
+_ORACLE = {}
+
+
+def oracle_solution(name, indices, energy="adiabatic"):
+    key = (name, tuple(indices), energy)
+    if key not in _ORACLE:
+        _, mech, batch = workload(name)
+        _ORACLE[key] = O.solve_batch(mech, batch, energy=energy, indices=list(indices))
+    return _ORACLE[key]
+
+
+def compare_roots(name, idx, ref, Y, T, st, what):
+    """Parity on reactors the oracle converged: same status, Y and T within the bar; a
+    different branch (|dT| > 1 K) counts only if the GPU state is a root of the oracle."""
+    _, mech, batch = workload(name)
+    n_ok = n_branch = 0
+    for j, b in enumerate(idx):
+        if ref["status"][j] != O.CONVERGED:
+            continue
+        assert st[j] == psr.PSR_CONVERGED, f"{what}: reactor {b} status {st[j]} (oracle converged)"
+        if abs(T[j] - ref["T"][j]) > 1.0:
+            F = O.gas_residual(mech, np.r_[Y[j], T[j]][None], O.inlet_of(batch, b))[0]
+            assert np.max(np.abs(F)) <= 1e-7, f"{what}: reactor {b} on another branch and not a root"
+            n_branch += 1
+            continue
+        big = ref["Y"][j] > Y_MIN
+        rel = np.max(np.abs(Y[j][big] - ref["Y"][j][big]) / ref["Y"][j][big])
+        assert rel <= Y_REL, f"{what}: reactor {b} Y rel err {rel:.3e}"
+        assert abs(T[j] - ref["T"][j]) <= T_ABS, f"{what}: reactor {b} T err {T[j] - ref['T'][j]:.3e}"
+        n_ok += 1
+    return n_ok, n_branch
+
+
+# ------------------------------------------------------------------ residual, Eqs. (2)-(9)
+@pytest.mark.parametrize("name", ["k10_b64", "k53_b4096"])
+@pytest.mark.parametrize("energy", ["adiabatic", "fixed"])
+def test_residual_parity(dev, name, energy):
+    import torch
+    _, mech, batch = workload(name)
+    m = 40
+    X = random_states(mech, m, seed=11, y_small=True)
+    sub = batch.subset(range(m))
+    t = to_dev(sub, dev)
+    Yd = torch.tensor(X[:, :-1], dtype=torch.float64, device=dev)
+    Td = torch.tensor(X[:, -1], dtype=torch.float64, device=dev)
+    e = psr.PSR_FIXED_T if energy == "fixed" else psr.PSR_ADIABATIC
+    F = psr.eval_residual(gpu_mech(name), t["Y_in"], t["T_in"], t["tau"], t["P"], Yd, Td, energy=e).cpu().numpy()
+    for b in range(m):
+        inlet = O.inlet_of(sub, b)
+        inlet.T_spec = X[b, -1]
+        Fo = O.gas_residual(mech, X[b][None], inlet, energy)[0]
+        # rounding scale: the gross production terms that cancel in each row
+        _, rho, C = O.mixture_state(mech, X[b:b + 1, :-1], X[b:b + 1, -1], inlet.P)
+        q = O.rates_of_progress(mech, X[b:b + 1, -1], C)[0]
+        gross = np.abs(mech.nu) @ np.abs(q) * inlet.tau * mech.W / rho[0]
+        scale = np.r_[1.0 + gross, 1.0 + np.max(np.abs(Fo)) + gross.max() * 50]
+        err = np.abs(F[b] - Fo) / scale
+        assert np.max(err) <= 1e-11, (b, np.argmax(err), F[b][np.argmax(err)], Fo[np.argmax(err)])
+
+
+# ------------------------------------------------------------------ Jacobian
+@pytest.mark.parametrize("name", ["k10_b64", "k53_b4096"])
+@pytest.mark.parametrize("precision", [psr.PSR_FP64, psr.PSR_MIXED])
+def test_jacobian_parity(dev, name, precision):
+    import torch
+    _, mech, batch = workload(name)
+    m = 12
+    X = random_states(mech, m, seed=12, y_small=True)
+    sub = batch.subset(range(m))
+    t = to_dev(sub, dev)
+    Yd = torch.tensor(X[:, :-1], dtype=torch.float64, device=dev)
+    Td = torch.tensor(X[:, -1], dtype=torch.float64, device=dev)
+    J = psr.eval_jacobian(gpu_mech(name), t["Y_in"], t["T_in"], t["tau"], t["P"], Yd, Td,
+                          precision=precision).cpu().numpy()
+    tol = 1e-8 if precision == psr.PSR_FP64 else 2e-5
+    for b in range(m):
+        S = O.GasSystem(mech, O.inlet_of(sub, b))
+        Jo = O.jacobian_cs(S, X[b])
+        rowmax = np.max(np.abs(Jo), axis=1, keepdims=True)
+        err = np.abs(J[b] - Jo) / rowmax
+        assert np.max(err) <= tol, (b, np.unravel_index(np.argmax(err), err.shape), np.max(err))
+
+
+# ------------------------------------------------------------------ LU
+@pytest.mark.parametrize("n", [1, 11, 33, 54, 64])
+def test_lu_parity(dev, n):
+    import torch
+    rng = np.random.Generator(np.random.PCG64(n))
+    B = 37
+    A = rng.standard_normal((B, n, n)) * np.exp(rng.uniform(-4, 4, (B, n, 1))) + 0 * np.eye(n)
+    r = rng.standard_normal((B, n))
+    x, ok = psr.batch_lu_solve(torch.tensor(A, device=dev), torch.tensor(r, device=dev), psr.PSR_FP64)
+    x, ok = x.cpu().numpy(), ok.cpu().numpy()
+    assert np.all(ok == 1)
+    for b in range(B):
+        LU, piv, good = O.lu_factor(A[b])
+        xo = O.lu_solve(LU, piv, r[b])
+        np.testing.assert_allclose(x[b], xo, rtol=1e-9, atol=1e-12 * np.abs(xo).max())
+    xm, okm = psr.batch_lu_solve(torch.tensor(A, device=dev), torch.tensor(r, device=dev), psr.PSR_MIXED)
+    xm = xm.cpu().numpy()
+    for b in range(B):
+        res = np.abs(A[b] @ xm[b] - r[b]).max() / (np.abs(A[b]).max() * np.abs(xm[b]).max() + np.abs(r[b]).max())
+        assert res <= 1e-5 * n
+
+
+def test_lu_singular(dev):
+    import torch
+    A = np.zeros((2, 3, 3))
+    A[0] = np.eye(3)
+    A[1] = [[1, 2, 3], [2, 4, 6], [1, 1, 1]]
+    x, ok = psr.batch_lu_solve(torch.tensor(A, device=dev), torch.ones((2, 3), dtype=torch.float64, device=dev))
+    assert ok.cpu().tolist() == [1, 0]
+
+
+# ------------------------------------------------------------------ full solves
+@pytest.mark.parametrize("precision", [psr.PSR_FP64, psr.PSR_MIXED])
+def test_solve_parity_k10_full_batch(dev, precision):
+    _, mech, batch = workload("k10_b64")
+    idx = list(range(batch.B))
+    ref = oracle_solution("k10_b64", idx)
+    t = to_dev(batch, dev)
+    out = psr.batch_solve(gpu_mech("k10_b64"), t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"],
+                          opts=psr.Options(precision=precision))
+    Y, T, st = out["Y"].cpu().numpy(), out["T"].cpu().numpy(), out["status"].cpu().numpy()
+    n_ok, n_branch = compare_roots("k10_b64", idx, ref, Y, T, st, f"k10 prec={precision}")
+    assert n_ok >= 0.9 * np.sum(ref["status"] == O.CONVERGED)
+    fn = out["fnorm"].cpu().numpy()
+    assert np.all(fn[st == 0] <= 1e-8)
+
+
+@pytest.mark.parametrize("precision", [psr.PSR_FP64, psr.PSR_MIXED])
+def test_solve_parity_k53_full_size_sampled(dev, precision):
+    """The B = 4096 launch the benchmark times; 6 sampled reactors against the oracle,
+    element conservation and ||F|| for every converged reactor."""
+    _, mech, batch = workload("k53_b4096")
+    t = to_dev(batch, dev)
+    out = psr.batch_solve(gpu_mech("k53_b4096"), t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"],
+                          opts=psr.Options(precision=precision))
+    Y, T, st = out["Y"].cpu().numpy(), out["T"].cpu().numpy(), out["status"].cpu().numpy()
+    conv = st == psr.PSR_CONVERGED
+    assert conv.mean() >= 0.8
+    assert np.all(out["fnorm"].cpu().numpy()[conv] <= 1e-8)
+    elem = ((Y[conv] - batch.Y_in[conv]) / mech.W) @ mech.comp
+    assert np.max(np.abs(elem)) <= 1e-12
+    idx = [int(i) for i in np.random.Generator(np.random.PCG64(5)).choice(batch.B, 6, replace=False)]
+    ref = oracle_solution("k53_b4096", idx)
+    compare_roots("k53_b4096", idx, ref, Y[idx], T[idx], st[idx], f"k53 prec={precision}")
+
+
+def test_fixed_temperature_closed_forms(dev):
+    """Golden isomerisation and dimerisation (fixed T) against their closed forms."""
+    import torch
+    mech = psr.Mechanism(golden_text("isomer_ab.psrmech"))
+    T, tau = 1500.0, 1e-3
+    Y_in = np.array([[0.5, 0.4, 0.1]])
+    args = [torch.tensor(v, dtype=torch.float64, device=dev) for v in
+            (Y_in, [500.0], [tau], [synth.ONE_ATM], Y_in, [T])]
+    for prec in (psr.PSR_FP64, psr.PSR_MIXED):
+        out = psr.batch_solve(mech, *args, opts=psr.Options(energy=psr.PSR_FIXED_T, precision=prec))
+        kf = 1000.0
+        kr = kf / math.exp((5.5 - 6.0) - (1500.0 - 2000.0) / T)
+        YA = (0.4 + tau * kr * 0.5) / (1 + tau * (kf + kr))
+        assert out["status"].item() == 0
+        np.testing.assert_allclose(out["Y"][0, 1].item(), YA, rtol=1e-12)
+        assert out["T"].item() == T
+
+
+def test_rate_multipliers(dev):
+    """rate_mult = 1 equals NULL; a perturbed multiplier vector matches the oracle's."""
+    import torch
+    _, mech, batch = workload("k10_b64")
+    idx = list(range(8))
+    sub = batch.subset(idx)
+    t = to_dev(sub, dev)
+    gm = gpu_mech("k10_b64")
+    a = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"])
+    ones = torch.ones(mech.I, dtype=torch.float64, device=dev)
+    b = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"], rate_mult=ones)
+    assert torch.equal(a["Y"], b["Y"]) and torch.equal(a["T"], b["T"])
+    lnm = np.random.Generator(np.random.PCG64(3)).uniform(-0.5, 0.5, mech.I)
+    c = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"],
+                        rate_mult=torch.tensor(np.exp(lnm), device=dev))
+    for j, bi in enumerate(idx):
+        r = O.solve_reactor(mech, O.inlet_of(sub, j), np.r_[sub.Y0[j], sub.T0[j]], lnmult=lnm)
+        if r.status == O.CONVERGED and c["status"][j].item() == 0 and abs(c["T"][j].item() - r.x[-1]) < 1:
+            big = r.x[:-1] > Y_MIN
+            Yg = c["Y"][j].cpu().numpy()
+            assert np.max(np.abs(Yg[big] - r.x[:-1][big]) / r.x[:-1][big]) <= Y_REL
+            assert abs(c["T"][j].item() - r.x[-1]) <= T_ABS
+
+
+def test_host_entry_matches_device(dev):
+    _, mech, batch = workload("k10_b64")
+    sub = batch.subset(range(16))
+    t = to_dev(sub, dev)
+    gm = gpu_mech("k10_b64")
+    a = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"])
+    h = psr.batch_solve_host(gm, sub.Y_in, sub.T_in, sub.tau, sub.P, sub.Y0, sub.T0)
+    np.testing.assert_array_equal(h["Y"], a["Y"].cpu().numpy())
+    np.testing.assert_array_equal(h["status"], a["status"].cpu().numpy())
+
+
+def test_edge_cases(dev):
+    import torch
+    _, mech, batch = workload("k10_b64")
+    gm = gpu_mech("k10_b64")
+    # empty batch: nothing launched, success
+    e = to_dev(batch.subset([]), dev)
+    out = psr.batch_solve(gm, e["Y_in"], e["T_in"], e["tau"], e["P"], e["Y0"], e["T0"])
+    assert out["Y"].shape == (0, mech.K)
+    # ragged sizes give the same per-reactor answers as the full batch
+    full = to_dev(batch, dev)
+    ref = psr.batch_solve(gm, full["Y_in"], full["T_in"], full["tau"], full["P"], full["Y0"], full["T0"])
+    for B in (1, 3, 33):
+        s = to_dev(batch.subset(range(B)), dev)
+        o = psr.batch_solve(gm, s["Y_in"], s["T_in"], s["tau"], s["P"], s["Y0"], s["T0"])
+        assert torch.equal(o["Y"], ref["Y"][:B]) and torch.equal(o["status"], ref["status"][:B])
+    # tau -> 0: outlet = inlet
+    s = to_dev(batch.subset(range(8)), dev)
+    s["tau"] = torch.full_like(s["tau"], 1e-20)
+    o = psr.batch_solve(gm, s["Y_in"], s["T_in"], s["tau"], s["P"], s["Y0"], s["T0"])
+    assert torch.all(o["status"] == 0)
+    torch.testing.assert_close(o["Y"], s["Y_in"], rtol=0, atol=1e-10)
+    torch.testing.assert_close(o["T"], s["T_in"], rtol=1e-9, atol=0)
+    # non-finite initial guess is reported per reactor, not as a call error
+    bad = {k: v.clone() for k, v in s.items()}
+    bad["T0"][2] = float("nan")
+    o = psr.batch_solve(gm, bad["Y_in"], bad["T_in"], bad["tau"], bad["P"], bad["Y0"], bad["T0"])
+    assert o["status"][2].item() == psr.PSR_NONFINITE
+    # invalid options are call errors
+    with pytest.raises(psr.PsrError):
+        psr.batch_solve(gm, s["Y_in"], s["T_in"], s["tau"], s["P"], s["Y0"], s["T0"], opts=psr.Options(ftol=-1))
