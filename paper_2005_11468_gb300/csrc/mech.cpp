@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -112,6 +113,7 @@ int parse(const std::string &text, Mech &m) {
     m.troe_row.assign(I, -1);
     m.eff_ptr.assign(I + 1, 0);
     std::vector<std::vector<std::pair<int, double>>> effs(I);
+    std::vector<std::array<double, 8>> troe_par(I);
     for (long i = 0; i < I; ++i) {
         if (!L.next(r) || r.size() < 4 || !to_i(r[0], v) || v != i)
             return bad("bad reaction record " + std::to_string(i));
@@ -177,8 +179,8 @@ int parse(const std::string &text, Mech &m) {
         if (m.type[i] == kTroe) {
             if (!has_low || !has_troe) return bad("falloff reaction " + std::to_string(i) + " needs low and troe");
             if (troe[1] <= 0 || troe[2] <= 0) return bad("falloff reaction " + std::to_string(i) + ": T3, T1 > 0");
-            m.troe_row[i] = m.n_troe++;
-            m.troe.insert(m.troe.end(), {std::log(low[0]), low[1], low[2], troe[0], troe[1], troe[2], troe[3], 0.0});
+            troe_par[i] = {std::log(low[0]), low[1], low[2], troe[0], troe[1], troe[2], troe[3], 0.0};
+            m.n_troe++;
         } else if (has_low || has_troe) {
             return bad("reaction " + std::to_string(i) + ": low/troe on a non-falloff reaction");
         }
@@ -200,6 +202,39 @@ int parse(const std::string &text, Mech &m) {
             return bad("unexpected record '" + r[0] + "'");
         }
     }
+    // Device order of the reactions: elementary, then third-body, then falloff, so that
+    // warps sweeping the reaction list meet one rate form per pass; orig maps back to
+    // the file's index (used for per-reaction inputs such as rate multipliers).
+    std::vector<int32_t> ord;
+    for (int want : {int(kElem), int(kThirdBody), int(kTroe)})
+        for (long i = 0; i < I; ++i)
+            if (m.type[i] == want) ord.push_back(static_cast<int32_t>(i));
+    {
+        auto perm = [&](auto &v, int width) {
+            auto old = v;
+            for (long i = 0; i < I; ++i)
+                for (int c = 0; c < width; ++c) v[i * width + c] = old[size_t(ord[i]) * width + c];
+        };
+        perm(m.lnA, 1);
+        perm(m.beta, 1);
+        perm(m.theta, 1);
+        perm(m.slots, 6);
+        perm(m.dnu, 1);
+        perm(m.type, 1);
+        auto e_old = effs;
+        auto t_old = troe_par;
+        for (long i = 0; i < I; ++i) {
+            effs[i] = e_old[ord[i]];
+            troe_par[i] = t_old[ord[i]];
+        }
+        m.orig = ord;
+    }
+    m.troe_first = static_cast<int>(I) - m.n_troe;
+    m.tb_first = m.troe_first - m.n_tb;
+    for (long i = m.troe_first; i < I; ++i) {
+        m.troe_row[i] = static_cast<int32_t>(i - m.troe_first);
+        m.troe.insert(m.troe.end(), troe_par[i].begin(), troe_par[i].end());
+    }
     // efficiency CSR
     for (long i = 0; i < I; ++i) {
         m.eff_ptr[i + 1] = m.eff_ptr[i] + static_cast<int32_t>(effs[i].size());
@@ -208,20 +243,30 @@ int parse(const std::string &text, Mech &m) {
             m.eff_val.push_back(e.second);
         }
     }
-    // distinct participants and net stoichiometry; species -> reaction CSR (Eq. (4))
+    // distinct participants, net stoichiometry and the slots each occupies;
+    // species -> reaction CSR (Eq. (4))
     m.part.assign(I * 6, static_cast<int16_t>(K));
     m.part_nu.assign(I * 6, 0);
+    m.part_fm.assign(I * 6, 0);
+    m.part_rm.assign(I * 6, 0);
     std::vector<std::vector<std::pair<int, int>>> by_sp(K);
     for (long i = 0; i < I; ++i) {
         std::map<int, int> nu;
+        std::map<int, int> fm, rm;
         for (int s = 0; s < 6; ++s) {
             int sp = m.slots[i * 6 + s];
-            if (sp < K) nu[sp] += (s < 3) ? -1 : 1;
+            if (sp < K) {
+                nu[sp] += (s < 3) ? -1 : 1;
+                if (s < 3) fm[sp] |= 1 << s;
+                else rm[sp] |= 1 << (s - 3);
+            }
         }
         int j = 0;
         for (auto &kv : nu) {
             m.part[i * 6 + j] = static_cast<int16_t>(kv.first);
             m.part_nu[i * 6 + j] = static_cast<int8_t>(kv.second);
+            m.part_fm[i * 6 + j] = static_cast<int8_t>(fm[kv.first]);
+            m.part_rm[i * 6 + j] = static_cast<int8_t>(rm[kv.first]);
             ++j;
             if (kv.second != 0) by_sp[kv.first].push_back({static_cast<int>(i), kv.second});
         }
@@ -250,7 +295,7 @@ int upload(Mech &m) {
     std::vector<double> invW(m.K);
     for (int k = 0; k < m.K; ++k) invW[k] = 1.0 / m.W[k];
     size_t oW, oinvW, onasa, olnA, obeta, otheta, oslots, odnu, otype, oeffp, oeffs, oeffv, otr, otroe,
-        osp, ospr, ospn, opart, opartnu;
+        osp, ospr, ospn, opart, opartnu, opfm, oprm, oorig;
     place(blob, m.W, oW);
     place(blob, invW, oinvW);
     place(blob, m.nasa, onasa);
@@ -270,6 +315,9 @@ int upload(Mech &m) {
     place(blob, m.sp_nu, ospn);
     place(blob, m.part, opart);
     place(blob, m.part_nu, opartnu);
+    place(blob, m.part_fm, opfm);
+    place(blob, m.part_rm, oprm);
+    place(blob, m.orig, oorig);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_error("cudaGetDevice", e);
@@ -308,6 +356,11 @@ int upload(Mech &m) {
     D.sp_nu = reinterpret_cast<const int8_t *>(b + ospn);
     D.part = reinterpret_cast<const int16_t *>(b + opart);
     D.part_nu = reinterpret_cast<const int8_t *>(b + opartnu);
+    D.part_fm = reinterpret_cast<const int8_t *>(b + opfm);
+    D.part_rm = reinterpret_cast<const int8_t *>(b + oprm);
+    D.orig = reinterpret_cast<const int32_t *>(b + oorig);
+    D.tb_first = m.tb_first;
+    D.troe_first = m.troe_first;
     return PSR_OK;
 }
 

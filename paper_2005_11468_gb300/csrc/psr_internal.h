@@ -33,10 +33,14 @@ struct DevMech {
     const int8_t *sp_nu;
     const int16_t *part;         // [I][6] distinct participants (K = none)
     const int8_t *part_nu;       // [I][6] net nu of each participant
+    const int8_t *part_fm;       // [I][6] bit s: participant fills reactant slot s
+    const int8_t *part_rm;       // [I][6] bit s: participant fills product slot s
+    const int32_t *orig;         // [I] index of the reaction in the mechanism file
+    int tb_first, troe_first;    // device order: elementary [0, tb_first), third-body, falloff [troe_first, I)
 };
 
 struct Mech {
-    int K = 0, I = 0, E = 0, n_tb = 0, n_troe = 0;
+    int K = 0, I = 0, E = 0, n_tb = 0, n_troe = 0, tb_first = 0, troe_first = 0;
     bool has_soot = false;
     std::vector<double> elem_w, W, comp;       // comp [K][E]
     std::vector<double> nasa;                  // [K][16]
@@ -52,7 +56,8 @@ struct Mech {
     std::vector<int16_t> sp_rxn;
     std::vector<int8_t> sp_nu;
     std::vector<int16_t> part;
-    std::vector<int8_t> part_nu;
+    std::vector<int8_t> part_nu, part_fm, part_rm;
+    std::vector<int32_t> orig;
     std::vector<double> soot;                  // raw soot constants (key order of the file)
     std::vector<std::string> soot_keys;
     int device = -1;

@@ -364,7 +364,7 @@ class Batch:
         return self.Y_in.shape[0]
 
     def subset(self, idx):
-        idx = np.asarray(idx)
+        idx = np.asarray(idx, dtype=np.int64)
         return Batch(*(getattr(self, f.name)[idx] for f in dataclasses.fields(self)))
 
 
