@@ -123,6 +123,24 @@ int psr_batch_solve(const psr_mech *m, int64_t B,
                     int32_t *iters, int32_t *ts_steps, int32_t *status, double *fnorm,
                     int32_t *nfev, const psr_options *opt, void *cuda_stream);
 
+/* psr_batch_solve for callers that cannot allocate device memory, e.g. code running
+ * where the allocator is frozen after start-up or only pre-registered buffers may be
+ * used. (The paper has no counterpart: this is a service of the library.) The call
+ * allocates nothing (no cudaMalloc, cudaMallocAsync or cudaFree): the solver's only
+ * scratch, its work-queue counter, sits in a static 256-byte device array that every
+ * GPU loading the library keeps until exit. Arguments, outputs and results are those
+ * of psr_batch_solve; B must not exceed 2^31 - 2^22 (PSR_E_ARG otherwise). The first
+ * call on each device looks up the array's device address (cudaGetSymbolAddress), so
+ * make that first call before any stream capture. All calls share the array: it is
+ * zeroed on the stream before each launch, and calls that overlap on the GPU (other
+ * streams, other host threads) race on it and must be serialised by the caller. */
+int psr_batch_solve_noalloc(const psr_mech *m, int64_t B,
+                            const double *Y_in, const double *T_in, const double *tau, const double *P,
+                            const double *Y0, const double *T0, const double *rate_mult,
+                            double *Y_out, double *T_out,
+                            int32_t *iters, int32_t *ts_steps, int32_t *status, double *fnorm,
+                            int32_t *nfev, const psr_options *opt, void *cuda_stream);
+
 /* Same as psr_batch_solve with every array in HOST memory: the call copies the inputs
  * to the device, solves, copies the outputs back and synchronises the stream before
  * returning. Device buffers are allocated and freed inside the call. */

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cfloat>
 #include <cmath>
 #include <cstdio>
@@ -1041,6 +1042,76 @@ int launch_eval(const Mech &m, const Batch &bt, int energy, int want_J, double *
     return PSR_OK;
 }
 
+// ---------------------------------------------------------------- allocation-free variant
+// Callers that may not allocate device memory (for example code running under an
+// allocator that is frozen after start-up, or a host that hands the library only
+// pre-registered buffers) use psr_batch_solve_noalloc. The only scratch the solver
+// kernel needs, its work-queue counter, then lives in this file-scope array, which
+// every GPU that loads the library keeps until the process exits. All calls share it:
+// it is zeroed on the stream before each launch, and calls that overlap on the GPU
+// race on it.
+constexpr int kNoAllocScratchInts = 64;                 // 256 bytes
+static __device__ __align__(256) int32_t g_noalloc_scratch[kNoAllocScratchInts];
+// largest batch whose work-queue counter (int32, overshot by at most one claim per
+// warp of the grid) cannot overflow
+constexpr int64_t kNoAllocMaxB = (int64_t(1) << 31) - (int64_t(1) << 22);
+
+constexpr int kMaxDevices = 64;
+std::atomic<int32_t *> g_noalloc_addr[kMaxDevices];
+
+// Device address of the scratch array on the current device: looked up once per device
+// (host code cannot take the address of a __device__ symbol directly).
+int noalloc_scratch(int32_t **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error("cudaGetDevice", e);
+    if (dev < 0 || dev >= kMaxDevices) return set_error(PSR_E_UNSUPPORTED, "device index too large");
+    int32_t *addr = g_noalloc_addr[dev].load();
+    if (!addr) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_error("cudaGetSymbolAddress(g_noalloc_scratch)", e);
+        addr = static_cast<int32_t *>(p);
+        g_noalloc_addr[dev].store(addr);
+    }
+    *out = addr;
+    return PSR_OK;
+}
+
+template <class TJ>
+int launch_solve_noalloc(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int bps_req, cudaStream_t st) {
+    int32_t *queue = nullptr;
+    int rc = noalloc_scratch(&queue);
+    if (rc != PSR_OK) return rc;
+    const size_t wsb = ws_bytes<TJ>(m.K, m.I, m.K + 1, m.n_troe);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int max_smem = 0, nsm = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int wpb = wpb_req > 0 ? wpb_req : 4;
+    while (wpb > 1 && size_t(wpb) * wsb > size_t(max_smem)) --wpb;
+    const size_t smem = size_t(wpb) * wsb;
+    if (smem > size_t(max_smem))
+        return set_error(PSR_E_UNSUPPORTED, "mechanism too large for one warp's shared memory");
+    cudaError_t e = cudaFuncSetAttribute(solve_kernel<TJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return cuda_error("cudaFuncSetAttribute", e);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel<TJ>, wpb * 32, smem);
+    if (e != cudaSuccess) return cuda_error("occupancy", e);
+    if (per_sm < 1) return set_error(PSR_E_UNSUPPORTED, "solver kernel does not fit on an SM");
+    if (bps_req > 0 && bps_req < per_sm) per_sm = bps_req;
+    int64_t want = (bt.B + wpb - 1) / wpb;
+    int64_t grid = std::min<int64_t>(int64_t(per_sm) * nsm, want);
+    if (grid < 1) grid = 1;
+    e = cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return cuda_error("cudaMemsetAsync(work queue)", e);
+    solve_kernel<TJ><<<unsigned(grid), wpb * 32, smem, st>>>(m.dev, bt, o, queue, wsb);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error("solve_kernel launch", e);
+    return PSR_OK;
+}
+
 int check_mech(const psr_mech *m) {
     if (!m) return set_error(PSR_E_ARG, "mechanism is NULL");
     if (m->m.K + 1 > kMaxWarpN)
@@ -1078,6 +1149,31 @@ int psr_batch_solve(const psr_mech *m, int64_t B, const double *Y_in, const doub
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (po.precision == PSR_MIXED) return launch_solve<float>(m->m, bt, o, po.warps_per_block, po.blocks_per_sm, st);
     return launch_solve<double>(m->m, bt, o, po.warps_per_block, po.blocks_per_sm, st);
+}
+
+int psr_batch_solve_noalloc(const psr_mech *m, int64_t B, const double *Y_in, const double *T_in, const double *tau,
+                            const double *P, const double *Y0, const double *T0, const double *rate_mult,
+                            double *Y_out, double *T_out, int32_t *iters, int32_t *ts_steps, int32_t *status,
+                            double *fnorm, int32_t *nfev, const psr_options *opt, void *cuda_stream) {
+    int rc = check_mech(m);
+    if (rc) return rc;
+    if (B < 0) return set_error(PSR_E_ARG, "B < 0");
+    if (B > kNoAllocMaxB)
+        return set_error(PSR_E_ARG, "psr_batch_solve_noalloc: B exceeds the static work-queue limit of " +
+                                        std::to_string(kNoAllocMaxB) + " reactors");
+    if (B == 0) return PSR_OK;
+    if (!Y_in || !T_in || !tau || !P || !Y0 || !T0 || !Y_out || !T_out)
+        return set_error(PSR_E_ARG, "psr_batch_solve_noalloc: required pointer is NULL");
+    if ((rc = check_opts(opt))) return rc;
+    Batch bt{B, Y_in, T_in, tau, P, Y0, T0, rate_mult, Y_out, T_out, fnorm, iters, ts_steps, status, nfev};
+    const Opts o = to_opts(opt);
+    psr_options d;
+    psr_options_default(&d);
+    const psr_options &po = opt ? *opt : d;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (po.precision == PSR_MIXED)
+        return launch_solve_noalloc<float>(m->m, bt, o, po.warps_per_block, po.blocks_per_sm, st);
+    return launch_solve_noalloc<double>(m->m, bt, o, po.warps_per_block, po.blocks_per_sm, st);
 }
 
 int psr_batch_solve_host(const psr_mech *m, int64_t B, const double *Y_in, const double *T_in, const double *tau,

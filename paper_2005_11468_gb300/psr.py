@@ -69,6 +69,7 @@ def lib():
         solve_args = [vp, i64] + [dp] * 7 + [dp] * 2 + [dp] * 5 + [ctypes.POINTER(COptions), vp]
         L.psr_batch_solve.argtypes = solve_args
         L.psr_batch_solve_host.argtypes = solve_args
+        L.psr_batch_solve_noalloc.argtypes = solve_args
         L.psr_eval_residual.argtypes = [vp, i64] + [dp] * 7 + [dp, i32, vp]
         L.psr_eval_jacobian.argtypes = [vp, i64] + [dp] * 7 + [dp, i32, i32, vp]
         L.psr_batch_lu_solve.argtypes = [i64, i32, dp, dp, dp, dp, i32, vp]
@@ -182,6 +183,31 @@ def batch_solve(mech: Mechanism, Y_in, T_in, tau, P, Y0, T0, rate_mult=None, opt
                    nfev=torch.empty(B, dtype=i32, device=dev))
     o = (opts or Options()).to_c()
     _check(lib().psr_batch_solve(
+        mech.handle, B, _ptr(Y_in, f64, (B, K), "Y_in"), _ptr(T_in, f64, (B,), "T_in"),
+        _ptr(tau, f64, (B,), "tau"), _ptr(P, f64, (B,), "P"), _ptr(Y0, f64, (B, K), "Y0"),
+        _ptr(T0, f64, (B,), "T0"), _ptr(rate_mult, f64, (mech.I,), "rate_mult"),
+        _ptr(out["Y"], f64, (B, K)), _ptr(out["T"], f64, (B,)), _ptr(out["iters"], i32, (B,)),
+        _ptr(out["ts_steps"], i32, (B,)), _ptr(out["status"], i32, (B,)), _ptr(out["fnorm"], f64, (B,)),
+        _ptr(out["nfev"], i32, (B,)), ctypes.byref(o), _stream()))
+    return out
+
+
+def batch_solve_noalloc(mech: Mechanism, Y_in, T_in, tau, P, Y0, T0, rate_mult=None, opts: Options = None,
+                        out=None):
+    """psr_batch_solve_noalloc: as batch_solve, but the library allocates no device memory
+    (its work-queue counter is a static device array). Output tensors must be passed in
+    `out` by callers that cannot allocate; otherwise they are created here."""
+    import torch
+    f64, i32 = torch.float64, torch.int32
+    B, K = Y_in.shape
+    dev = Y_in.device
+    if out is None:
+        out = dict(Y=torch.empty((B, K), dtype=f64, device=dev), T=torch.empty(B, dtype=f64, device=dev),
+                   iters=torch.empty(B, dtype=i32, device=dev), ts_steps=torch.empty(B, dtype=i32, device=dev),
+                   status=torch.empty(B, dtype=i32, device=dev), fnorm=torch.empty(B, dtype=f64, device=dev),
+                   nfev=torch.empty(B, dtype=i32, device=dev))
+    o = (opts or Options()).to_c()
+    _check(lib().psr_batch_solve_noalloc(
         mech.handle, B, _ptr(Y_in, f64, (B, K), "Y_in"), _ptr(T_in, f64, (B,), "T_in"),
         _ptr(tau, f64, (B,), "tau"), _ptr(P, f64, (B,), "P"), _ptr(Y0, f64, (B, K), "Y0"),
         _ptr(T0, f64, (B,), "T0"), _ptr(rate_mult, f64, (mech.I,), "rate_mult"),
