@@ -169,6 +169,21 @@ int psr_eval_jacobian(const psr_mech *m, int64_t B,
                       const double *Y, const double *T, const double *rate_mult,
                       double *J_out, int32_t energy, int32_t precision, void *cuda_stream);
 
+/* Adjoint sensitivities of the steady state to the rate multipliers: for a loss L with
+ * g = dL/dx at converged states x = (Y [B][K], T [B]) of the problem in psr_eval_residual,
+ * grad_out [B][I] (reaction order of the mechanism file) receives
+ *   dL/d ln m_i = g^T dx/d ln m_i = -lambda^T dF/d ln m_i,  J^T lambda = g,
+ * by the implicit function theorem at F(x) = 0 (the steady balances of Sec. 2 with the
+ * rates of Sec. 3; m_i multiplies q_i). J is the FP64 analytic Jacobian factored by the
+ * solver's LU; lambda_out [B][K+1] (nullable) receives lambda, ok_out [B] (nullable)
+ * 1 when J factored (0: gradient set to 0). g [B][K+1] rows are (dL/dY_1..dL/dY_K, dL/dT).
+ * Errors: PSR_E_ARG, PSR_E_UNSUPPORTED (K + 1 > 64), PSR_E_CUDA. */
+int psr_batch_adjoint(const psr_mech *m, int64_t B,
+                      const double *Y_in, const double *T_in, const double *tau, const double *P,
+                      const double *Y, const double *T, const double *rate_mult, const double *g,
+                      double *grad_out, double *lambda_out, int32_t *ok_out, int32_t energy,
+                      void *cuda_stream);
+
 /* Batched dense solve A_b x_b = r_b by the solver's LU with partial pivoting
  * (Sec. 1, Sec. 3): A [B][n][n] row-major, r [B][n], x_out [B][n], ok_out [B]
  * (1 = factored, 0 = zero or non-finite pivot), n <= 64. PSR_MIXED factors in FP32. */

@@ -244,7 +244,7 @@ def rates_of_progress(mech: Mechanism, T, C, lnmult=None):
     q = kf * fwd - kr * rev
     q = np.where(mech.is_tb[None], q * M, q)
     if lnmult is not None:
-        q = q * np.exp(np.asarray(lnmult, dtype=np.float64))
+        q = q * np.exp(_arr(lnmult))
     return q
 
 
@@ -568,3 +568,33 @@ def solve_batch(mech: Mechanism, batch, opts: Options = Options(), energy="adiab
         out["status"].append(r.status); out["iters"].append(r.iters)
         out["ts_steps"].append(r.ts_steps); out["fnorm"].append(r.fnorm)
     return {k: np.array(v) for k, v in out.items()}
+
+
+# ----------------------------------------------------------------------------- sensitivities
+def rate_parameter_jacobian(mech: Mechanism, inlet: Inlet, x, energy="adiabatic", lnmult=None, h=1e-30):
+    """dF/dp at state x for p_i = ln(multiplier of q_i), one complex-step column per
+    reaction (the multiplier scales the whole rate of progress of reaction i)."""
+    I = mech.I
+    base = np.zeros(I) if lnmult is None else np.asarray(lnmult, dtype=np.float64)
+    P = np.repeat(base[None].astype(np.complex128), I, axis=0)
+    P[np.arange(I), np.arange(I)] += 1j * h
+    X = np.repeat(np.asarray(x, dtype=np.complex128)[None], I, axis=0)
+    Fp = gas_residual(mech, X, inlet, energy, P)
+    return (Fp.imag / h).T                        # (n, I)
+
+
+def sensitivities(mech: Mechanism, inlet: Inlet, x, energy="adiabatic", lnmult=None):
+    """Dense S = dx*/dp = -J^-1 dF/dp at a root x* (implicit function theorem), with the
+    complex-step Jacobian and the oracle's own LU."""
+    S_sys = GasSystem(mech, inlet, energy, lnmult)
+    J = jacobian_cs(S_sys, x)
+    Fp = rate_parameter_jacobian(mech, inlet, x, energy, lnmult)
+    LU, piv, ok = lu_factor(J)
+    if not ok:
+        raise ArithmeticError("singular Jacobian at the root")
+    return -np.stack([lu_solve(LU, piv, Fp[:, i]) for i in range(mech.I)], axis=1)
+
+
+def adjoint_gradient(mech: Mechanism, inlet: Inlet, x, g, energy="adiabatic", lnmult=None):
+    """dL/dp_i = g^T dx*/dp_i for a loss with dL/dx* = g, from the dense sensitivities."""
+    return np.asarray(g, dtype=np.float64) @ sensitivities(mech, inlet, x, energy, lnmult)

@@ -610,6 +610,41 @@ __device__ PSR_STAGE void lu_solve_neg(const WS<TJ> &w, int n, const V2 &r, V2 &
     __syncwarp();
 }
 
+// Solve J^T lam = g with the factors of P J = L U: U^T z = g (forward), L^T v = z
+// (backward, unit diagonal), lam[perm[j]] = v[j]. g and lam are distributed (V2).
+template <class TJ>
+__device__ void lu_solve_T(const WS<TJ> &w, int n, const V2 &g, V2 &lam) {
+    const int lane = threadIdx.x & 31;
+    const int P = w.P;
+    for (int h = 0; h < 2; ++h) {
+        int j = lane + 32 * h;
+        if (j < n) w.rhs[j] = TJ(h ? g.b : g.a);
+    }
+    __syncwarp();
+    for (int k = 0; k < n; ++k) {
+        const TJ zk = w.rhs[k] / w.J[size_t(k) * P + k];
+        __syncwarp();
+        for (int j = k + 1 + lane; j < n; j += 32) w.rhs[j] = fma(-w.J[size_t(k) * P + j], zk, w.rhs[j]);
+        if (lane == 0) w.rhs[k] = zk;
+        __syncwarp();
+    }
+    for (int k = n - 1; k >= 1; --k) {
+        const TJ vk = w.rhs[k];
+        for (int j = lane; j < k; j += 32) w.rhs[j] = fma(-w.J[size_t(k) * P + j], vk, w.rhs[j]);
+        __syncwarp();
+    }
+    // lam_c = v_j for the j with perm[j] = c
+    double out[2] = {0.0, 0.0};
+    for (int j = 0; j < n; ++j) {
+        const int c = w.perm[j];
+        if (c == lane) out[0] = double(w.rhs[j]);
+        if (c == lane + 32) out[1] = double(w.rhs[j]);
+    }
+    lam.a = out[0];
+    lam.b = out[1];
+    __syncwarp();
+}
+
 // ---------------------------------------------------------------- solver pieces
 struct Reactor {
     const double *Yin;
@@ -927,6 +962,84 @@ __global__ void eval_kernel(DevMech M, Batch bt, int energy, int want_J, double 
     eval_J(M, w, y, zero, cx.mx, cx.sl, cx.r.Yin, cx.r.tau, energy, cx.mult);
     for (int idx = lane; idx < n * n; idx += 32)
         out[r * n * n + idx] = double(w.J[size_t(idx / n) * w.P + idx % n]);
+}
+
+// Adjoint sensitivities at given (converged) states, one warp per reactor: FP64
+// Jacobian, transposed LU solve J^T lam = g, then per reaction
+// dL/d ln m_i = -lam . dF/d ln m_i = (tau q_i / rho) [sum_k lam_k W_k nu_ki - lam_T dH_i / (c_p T)].
+__global__ void adjoint_kernel(DevMech M, Batch bt, int energy, const double *g, double *grad, double *lam_out,
+                               int32_t *ok, size_t ws_per_warp) {
+    extern __shared__ __align__(16) char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r = int64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
+    if (r >= bt.B) return;
+    WS<double> w = carve<double>(smem + warp * ws_per_warp, M.K, M.I, M.K + 1, M.n_troe);
+    Ctx cx;
+    cx.M = M;
+    cx.mult = bt.rate_mult;
+    cx.K = M.K;
+    cx.n = M.K + 1;
+    cx.o.energy = energy;
+    const int K = M.K, n = K + 1, I = M.I;
+    cx.r.Yin = bt.Y_in + r * K;
+    cx.r.tau = bt.tau[r];
+    cx.r.P = bt.P[r];
+    cx.r.Tspec = bt.T0[r];
+    {
+        const double Tin = bt.T_in[r], lnTin = log(Tin);
+        double s = 0.0;
+        for (int h = 0; h < 2; ++h) {
+            int j = lane + 32 * h;
+            if (j < K) {
+                double cpR, hRT, sR, dcpR;
+                nasa7(M.nasa, j, Tin, lnTin, 1.0 / Tin, cpR, hRT, sR, dcpR);
+                s += cx.r.Yin[j] * hRT * __ldg(M.invW + j);
+            }
+        }
+        cx.mx.h_in = wsum(s) * kRu * Tin;
+    }
+    V2 y;
+    y.a = (lane < K) ? bt.Y0[r * K + lane] : (lane == K ? bt.T0[r] : 0.0);
+    y.b = (lane + 32 < K) ? bt.Y0[r * K + lane + 32] : (lane + 32 == K ? bt.T0[r] : 0.0);
+    const V2 zero{0.0, 0.0};
+    V2 F, R;
+    residual_R(cx, w, y, zero, y, F, R);
+    eval_J(M, w, y, zero, cx.mx, cx.sl, cx.r.Yin, cx.r.tau, energy, cx.mult);
+    const bool good = lu_factor(w, n);
+    V2 gv, lam{0.0, 0.0};
+    gv.a = (lane < n) ? g[r * n + lane] : 0.0;
+    gv.b = (lane + 32 < n) ? g[r * n + lane + 32] : 0.0;
+    if (good) lu_solve_T(w, n, gv, lam);
+    // the Jacobian pass replaced q_i: evaluate the residual once more to restore it
+    residual_R(cx, w, y, zero, y, F, R);
+    if (lam_out) {
+        if (lane < n) lam_out[r * n + lane] = lam.a;
+        if (lane + 32 < n) lam_out[r * n + lane + 32] = lam.b;
+    }
+    // stage lam_k W_k (species) in v[] and lam_T in registers
+    const double lamT = comp_get(lam, K);
+    for (int h = 0; h < 2; ++h) {
+        int j = lane + 32 * h;
+        if (j < K) w.v[j] = (h ? lam.b : lam.a) * __ldg(M.W + j);
+    }
+    __syncwarp();
+    const double tau_rho = cx.r.tau / cx.mx.rho;
+    const double eT = (energy == PSR_FIXED_T) ? 0.0 : lamT * kRu * cx.mx.T / (cx.mx.cp * cx.mx.T);
+    for (int i = lane; i < I; i += 32) {
+        const int16_t *pp = M.part + size_t(i) * 6;
+        const int8_t *pn = M.part_nu + size_t(i) * 6;
+        double lw = 0.0, dH = 0.0;
+        for (int t = 0; t < 6; ++t) {
+            const int l = __ldg(pp + t);
+            if (l >= K) continue;
+            const double nu = double(__ldg(pn + t));
+            lw += nu * w.v[l];
+            dH += nu * w.hRT[l];
+        }
+        const double gi = good ? tau_rho * w.q[i] * (lw - eT * dH) : 0.0;
+        grad[r * I + __ldg(M.orig + i)] = gi;
+    }
+    if (ok && lane == 0) ok[r] = good ? 1 : 0;
 }
 
 template <class TJ>
@@ -1252,6 +1365,30 @@ int psr_eval_jacobian(const psr_mech *m, int64_t B, const double *Y_in, const do
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (precision == PSR_MIXED) return launch_eval<float>(m->m, bt, energy, 1, J_out, st);
     return launch_eval<double>(m->m, bt, energy, 1, J_out, st);
+}
+
+int psr_batch_adjoint(const psr_mech *m, int64_t B, const double *Y_in, const double *T_in, const double *tau,
+                      const double *P, const double *Y, const double *T, const double *rate_mult, const double *g,
+                      double *grad_out, double *lambda_out, int32_t *ok_out, int32_t energy, void *cuda_stream) {
+    int rc = check_mech(m);
+    if (rc) return rc;
+    if (B < 0 || (energy != PSR_ADIABATIC && energy != PSR_FIXED_T)) return set_error(PSR_E_ARG, "bad B or energy");
+    if (B == 0) return PSR_OK;
+    if (!Y_in || !T_in || !tau || !P || !Y || !T || !g || !grad_out)
+        return set_error(PSR_E_ARG, "psr_batch_adjoint: required pointer is NULL");
+    Batch bt{B, Y_in, T_in, tau, P, Y, T, rate_mult, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    const Mech &mm = m->m;
+    const size_t wsb = ws_bytes<double>(mm.K, mm.I, mm.K + 1, mm.n_troe);
+    const int wpb = 2;
+    const size_t smem = wpb * wsb;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return cuda_error("cudaFuncSetAttribute", e);
+    const int64_t grid = (B + wpb - 1) / wpb;
+    adjoint_kernel<<<unsigned(grid), wpb * 32, smem, st>>>(mm.dev, bt, energy, g, grad_out, lambda_out, ok_out, wsb);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error("adjoint_kernel launch", e);
+    return PSR_OK;
 }
 
 int psr_batch_lu_solve(int64_t B, int32_t n, const double *A, const double *r, double *x_out, int32_t *ok_out,

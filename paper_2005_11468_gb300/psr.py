@@ -73,6 +73,7 @@ def lib():
         L.psr_eval_residual.argtypes = [vp, i64] + [dp] * 7 + [dp, i32, vp]
         L.psr_eval_jacobian.argtypes = [vp, i64] + [dp] * 7 + [dp, i32, i32, vp]
         L.psr_batch_lu_solve.argtypes = [i64, i32, dp, dp, dp, dp, i32, vp]
+        L.psr_batch_adjoint.argtypes = [vp, i64] + [dp] * 7 + [dp, dp, dp, dp, i32, vp]
         _lib = L
     return _lib
 
@@ -283,3 +284,19 @@ def batch_lu_solve(A, r, precision=PSR_FP64):
     _check(lib().psr_batch_lu_solve(B, n, _ptr(A, torch.float64, (B, n, n), "A"), _ptr(r, torch.float64, (B, n), "r"),
                                     x.data_ptr(), ok.data_ptr(), precision, _stream()))
     return x, ok
+
+
+def batch_adjoint(mech: Mechanism, Y_in, T_in, tau, P, Y, T, g, rate_mult=None, energy=PSR_ADIABATIC):
+    """psr_batch_adjoint: dL/d ln(rate multiplier) [B, I] for dL/d(Y, T) = g [B, K+1] at
+    converged states. Returns (grad, lambda, ok)."""
+    import torch
+    f64 = torch.float64
+    B, K = Y.shape
+    grad = torch.empty((B, mech.I), dtype=f64, device=Y.device)
+    lam = torch.empty((B, K + 1), dtype=f64, device=Y.device)
+    ok = torch.empty(B, dtype=torch.int32, device=Y.device)
+    _check(lib().psr_batch_adjoint(
+        mech.handle, B, _ptr(Y_in, f64, (B, K)), _ptr(T_in, f64, (B,)), _ptr(tau, f64, (B,)),
+        _ptr(P, f64, (B,)), _ptr(Y, f64, (B, K)), _ptr(T, f64, (B,)), _ptr(rate_mult, f64, (mech.I,)),
+        _ptr(g, f64, (B, K + 1), "g"), grad.data_ptr(), lam.data_ptr(), ok.data_ptr(), energy, _stream()))
+    return grad, lam, ok
