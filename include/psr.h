@@ -97,7 +97,7 @@ typedef struct {
     int32_t ts_newton;      /* 8: Newton iterations per pseudo-time step */
     int32_t precision;      /* PSR_FP64 (default) or PSR_MIXED */
     int32_t energy;         /* PSR_ADIABATIC (default) or PSR_FIXED_T */
-    int32_t warps_per_block;/* 0 = tuned default */
+    int32_t warps_per_block;/* 0 = default (2); at most 4 */
     int32_t blocks_per_sm;  /* 0 = as many as fit */
     int32_t reserved[7];
 } psr_options;

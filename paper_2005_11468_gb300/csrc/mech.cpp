@@ -295,7 +295,8 @@ int upload(Mech &m) {
     std::vector<double> invW(m.K);
     for (int k = 0; k < m.K; ++k) invW[k] = 1.0 / m.W[k];
     size_t oW, oinvW, onasa, olnA, obeta, otheta, oslots, odnu, otype, oeffp, oeffs, oeffv, otr, otroe,
-        osp, ospr, ospn, opart, opartnu, opfm, oprm, oorig;
+        osp, ospr, ospn, opart, opartnu, opfm, oprm, oorig, odnud, ospnd;
+    std::vector<double> dnu_d(m.dnu.begin(), m.dnu.end()), sp_nu_d(m.sp_nu.begin(), m.sp_nu.end());
     place(blob, m.W, oW);
     place(blob, invW, oinvW);
     place(blob, m.nasa, onasa);
@@ -318,6 +319,8 @@ int upload(Mech &m) {
     place(blob, m.part_fm, opfm);
     place(blob, m.part_rm, oprm);
     place(blob, m.orig, oorig);
+    place(blob, dnu_d, odnud);
+    place(blob, sp_nu_d, ospnd);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_error("cudaGetDevice", e);
@@ -359,6 +362,8 @@ int upload(Mech &m) {
     D.part_fm = reinterpret_cast<const int8_t *>(b + opfm);
     D.part_rm = reinterpret_cast<const int8_t *>(b + oprm);
     D.orig = reinterpret_cast<const int32_t *>(b + oorig);
+    D.dnu_d = reinterpret_cast<const double *>(b + odnud);
+    D.sp_nu_d = reinterpret_cast<const double *>(b + ospnd);
     D.tb_first = m.tb_first;
     D.troe_first = m.troe_first;
     return PSR_OK;

@@ -22,6 +22,7 @@ struct DevMech {
     const double *lnA, *beta, *theta;   // [I] Eq. (6), E/R in K
     const int16_t *slots;        // [I][6] reactant slots 0..2, product slots 3..5, K = empty
     const int8_t *dnu;           // [I] sum_k nu_ki
+    const double *dnu_d;         // [I] the same as double
     const int8_t *type;          // [I] RxnType
     const int32_t *eff_ptr;      // [I+1] CSR of (efficiency - 1) for tb/troe rows
     const int16_t *eff_sp;       // [n_eff]
@@ -31,6 +32,7 @@ struct DevMech {
     const int32_t *sp_ptr;       // [K+1] CSR species -> reactions for wdot_k = sum nu_ki q_i
     const int16_t *sp_rxn;
     const int8_t *sp_nu;
+    const double *sp_nu_d;       // sp_nu as double
     const int16_t *part;         // [I][6] distinct participants (K = none)
     const int8_t *part_nu;       // [I][6] net nu of each participant
     const int8_t *part_fm;       // [I][6] bit s: participant fills reactant slot s
