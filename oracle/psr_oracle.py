@@ -368,32 +368,32 @@ class GasSystem:
         return gas_residual(self.mech, X, self.inlet, self.energy, self.lnmult)
 
     def fd_scale(self, x):
-        s = np.full(self.n, 0.1)
+        s = np.full(self.K + 1, 0.1)
         s[self.K] = 1000.0
         return s
 
     def step_tol(self, x, opts):
-        atol = np.full(self.n, opts.step_atol_y)
+        atol = np.full(self.K + 1, opts.step_atol_y)
         atol[self.K] = opts.step_atol_t
         return opts.step_rtol * np.abs(x) + atol
 
     def ts_tol(self, x, opts):
-        atol = np.full(self.n, opts.ts_atol_y)
+        atol = np.full(self.K + 1, opts.ts_atol_y)
         atol[self.K] = opts.ts_rtol
         return opts.ts_rtol * np.abs(x) + atol
 
     def norm_weights(self, x):
         """Scaling of the step norm: mass fractions absolute, temperature relative."""
-        w = np.ones(self.n)
+        w = np.ones(self.K + 1)
         w[self.K] = 1.0 / abs(x[self.K])
         return w
 
     def max_in_bounds(self, x, dx, opts):
         """Largest lambda with x + lambda dx inside the bounds (inf if unlimited)."""
         lam = math.inf
-        lo = np.full(self.n, -opts.y_floor); hi = np.full(self.n, math.inf)
+        lo = np.full(self.K + 1, -opts.y_floor); hi = np.full(self.K + 1, math.inf)
         lo[self.K], hi[self.K] = opts.t_min, opts.t_max
-        for j in range(self.n):
+        for j in range(self.K + 1):
             if dx[j] < 0 and x[j] + dx[j] < lo[j]:
                 lam = min(lam, (lo[j] - x[j]) / dx[j])
             elif dx[j] > 0 and x[j] + dx[j] > hi[j]:
@@ -407,7 +407,7 @@ class GasSystem:
     def transient_weights(self, x):
         """Inverse mass-matrix diagonal of the pseudo-transient form dx/dt = -D F / tau:
         1 for the species rows, 1/T for the (dimensionless) energy row."""
-        w = np.ones(self.n)
+        w = np.ones(self.K + 1)
         if self.energy != "fixed":
             w[self.K] = 1.0 / x[self.K]
         return w

@@ -301,14 +301,14 @@ def make_mechanism(K, I, n_tb=0, n_troe=0, seed=MECH_SEED_BASE, soot=False, spli
     if soot:
         soot_p = dict(
             precursor=3, h2=2,
-            nuc_A=float(10.0 ** rng.uniform(8.5, 9.5)),    # 1/s on precursor concentration
-            nuc_theta=float(rng.uniform(15000.0, 20000.0)),
-            cmin=32.0,                                     # carbon atoms per nucleus
-            grow_A=float(10.0 ** rng.uniform(11.5, 12.5)),  # cm^3/(mol s) per active site
+            nuc_A=float(10.0 ** rng.uniform(5.0, 6.0)),       # 1/s on the precursor concentration
+            nuc_theta=float(rng.uniform(10000.0, 14000.0)),
+            cmin=32.0,                                         # carbon atoms per nucleus
+            grow_A=float(10.0 ** rng.uniform(13.0, 14.0)),     # cm^3/(mol s) per active site
             grow_beta=0.0,
-            grow_theta=float(rng.uniform(5000.0, 7000.0)),
-            chi_alpha=float(rng.uniform(1e13, 5e14)),       # active sites per cm^2 x alpha
-            rho_s=1.8, coag_eps=2.2, m0_floor=1.0, scale_floor=1e-6,
+            grow_theta=float(rng.uniform(3000.0, 6000.0)),
+            chi_alpha=float(rng.uniform(1e13, 5e14)),          # active sites per cm^2 x alpha
+            rho_s=1.8, coag_eps=2.2, m0_floor=1.0,
         )
     return MechanismSpec(names, comp, t_range, low, high, reactions, soot_p)
 
@@ -358,6 +358,7 @@ class Batch:
     P: np.ndarray
     Y0: np.ndarray
     T0: np.ndarray
+    M_in: Optional[np.ndarray] = None      # [B][6] inlet soot moments (sooting mechanisms)
 
     @property
     def B(self):
@@ -365,7 +366,11 @@ class Batch:
 
     def subset(self, idx):
         idx = np.asarray(idx, dtype=np.int64)
-        return Batch(*(getattr(self, f.name)[idx] for f in dataclasses.fields(self)))
+        return Batch(*(None if getattr(self, f.name) is None else getattr(self, f.name)[idx]
+                       for f in dataclasses.fields(self)))
+
+
+SEED_PARTICLES = 1e-6      # nuclei per cm^3 in the inlet of a sooting batch (a trace of seeds)
 
 
 def make_batch(m: MechanismSpec, B, seed, tau_range=(1e-4, 1e-2), T_in_range=(300.0, 800.0),
@@ -379,7 +384,11 @@ def make_batch(m: MechanismSpec, B, seed, tau_range=(1e-4, 1e-2), T_in_range=(30
     T_in = rng.uniform(*T_in_range, B)
     tau = np.exp(rng.uniform(np.log(tau_range[0]), np.log(tau_range[1]), B))
     P = np.full(B, ONE_ATM)
-    return Batch(Y_in, T_in, tau, P, Y_in.copy(), np.full(B, float(T_guess)))
+    b = Batch(Y_in, T_in, tau, P, Y_in.copy(), np.full(B, float(T_guess)))
+    if m.soot is not None:
+        # inlet moments of SEED_PARTICLES nuclei of C_min carbon atoms: M_r = N C_min^r
+        b.M_in = np.tile(SEED_PARTICLES * m.soot["cmin"] ** np.arange(6.0), (B, 1))
+    return b
 
 
 # Named workloads (shapes of the paper's batched runs, scaled to the synthetic mechanisms).
