@@ -47,6 +47,8 @@ extern "C" {
 #define PSR_MAX_ITER 1      /* max_newton Newton iterations used */
 #define PSR_NONFINITE 2     /* the residual at the initial guess is not finite */
 #define PSR_TS_EXHAUSTED 4  /* max_ts_rounds time-stepping rounds, or dt collapsed */
+#define PSR_REFINE_FALLBACK 5 /* PSR_MIXED: converged (same criterion) after the FP32-Jacobian
+                                 launch left it unconverged and the FP64 re-solve succeeded */
 
 /* precision of the Jacobian and its LU factors (the residual is always FP64) */
 #define PSR_FP64 0
@@ -99,7 +101,8 @@ typedef struct {
     int32_t energy;         /* PSR_ADIABATIC (default) or PSR_FIXED_T */
     int32_t warps_per_block;/* 0 = default (2); at most 4 */
     int32_t blocks_per_sm;  /* 0 = as many as fit */
-    int32_t reserved[7];
+    int32_t mixed_fallback; /* 1 (default): PSR_MIXED re-solves unconverged reactors in FP64 */
+    int32_t reserved[6];
 } psr_options;
 
 void psr_options_default(psr_options *o);
@@ -113,8 +116,14 @@ void psr_options_default(psr_options *o);
  *   Y_out [B][K], T_out [B]: final iterates (the root for PSR_CONVERGED reactors).
  *   iters [B], ts_steps [B], status [B], fnorm [B] (||F||_inf at the output state),
  *   nfev [B] (residual evaluations, the reactor's share of the FP64 work): each may be NULL.
- * One persistent kernel launch; reactors are taken from a work queue by warps.
- * Device memory: a small work-queue counter is allocated and freed on the stream.
+ * One persistent kernel launch; reactors are taken from a work queue by warps. With
+ * PSR_MIXED and mixed_fallback = 1 a second launch re-solves, from Y0/T0 and with the
+ * FP64 Jacobian, the reactors the first left unconverged (the list is built on the
+ * device; no host synchronisation); their counters add up and a success reports
+ * PSR_REFINE_FALLBACK. If Y0/T0 alias Y_out/T_out, that re-solve starts from the first
+ * launch's final iterate.
+ * Device memory: a few scratch integers (B + 4 for the fallback, B more when status is
+ * NULL) are allocated and freed on the stream.
  * Errors: PSR_E_ARG, PSR_E_UNSUPPORTED (K + 1 > 64 for this kernel), PSR_E_CUDA. */
 int psr_batch_solve(const psr_mech *m, int64_t B,
                     const double *Y_in, const double *T_in, const double *tau, const double *P,
@@ -129,7 +138,9 @@ int psr_batch_solve(const psr_mech *m, int64_t B,
  * allocates nothing (no cudaMalloc, cudaMallocAsync or cudaFree): the solver's only
  * scratch, its work-queue counter, sits in a static 256-byte device array that every
  * GPU loading the library keeps until exit. Arguments, outputs and results are those
- * of psr_batch_solve; B must not exceed 2^31 - 2^22 (PSR_E_ARG otherwise). The first
+ * of psr_batch_solve, except that PSR_MIXED runs the single FP32-Jacobian launch (no
+ * FP64 fallback, mixed_fallback is ignored); B must not exceed 2^31 - 2^22 (PSR_E_ARG
+ * otherwise). The first
  * call on each device looks up the array's device address (cudaGetSymbolAddress), so
  * make that first call before any stream capture. All calls share the array: it is
  * zeroed on the stream before each launch, and calls that overlap on the GPU (other
@@ -140,6 +151,34 @@ int psr_batch_solve_noalloc(const psr_mech *m, int64_t B,
                             double *Y_out, double *T_out,
                             int32_t *iters, int32_t *ts_steps, int32_t *status, double *fnorm,
                             int32_t *nfev, const psr_options *opt, void *cuda_stream);
+
+/* Gas + MOMIC soot PSR (mechanisms with a soot record): the K + 1 gas balances plus six
+ * moment balances F_r = (M_r - M_r,in - tau (R_r + W_r + G_r)) / (M_r + s_r) of the soot
+ * moments M_0..M_5 (nucleation, surface growth and free-molecular coagulation of the
+ * method of moments with interpolative closure that the paper couples to its PSR,
+ * Abstract, Secs. 1, 5 and 7), solved for (Y, T, ln(M / s)).
+ *   M_in [B][6] inlet moments (particles/cm^3 x carbon atoms^r, > 0), M0 [B][6] initial
+ *   moments or NULL (then the nucleation-only steady state at the initial gas state),
+ *   M_out [B][6] output moments; other arguments as psr_batch_solve. K + 7 <= 64. */
+int psr_batch_solve_soot(const psr_mech *m, int64_t B,
+                         const double *Y_in, const double *T_in, const double *tau, const double *P,
+                         const double *M_in, const double *Y0, const double *T0, const double *M0,
+                         const double *rate_mult, double *Y_out, double *T_out, double *M_out,
+                         int32_t *iters, int32_t *ts_steps, int32_t *status, double *fnorm,
+                         int32_t *nfev, const psr_options *opt, void *cuda_stream);
+
+/* Residual [B][K+7] (gas rows as psr_eval_residual, then the six moment rows) and its
+ * Jacobian [B][K+7][K+7] at states (Y, T, moments M [B][6]) of a sooting mechanism. The
+ * soot-source columns of the Jacobian are central differences of the source function. */
+int psr_eval_residual_soot(const psr_mech *m, int64_t B,
+                           const double *Y_in, const double *T_in, const double *tau, const double *P,
+                           const double *M_in, const double *Y, const double *T, const double *M,
+                           const double *rate_mult, double *F_out, int32_t energy, void *cuda_stream);
+int psr_eval_jacobian_soot(const psr_mech *m, int64_t B,
+                           const double *Y_in, const double *T_in, const double *tau, const double *P,
+                           const double *M_in, const double *Y, const double *T, const double *M,
+                           const double *rate_mult, double *J_out, int32_t energy, int32_t precision,
+                           void *cuda_stream);
 
 /* Same as psr_batch_solve with every array in HOST memory: the call copies the inputs
  * to the device, solves, copies the outputs back and synchronises the stream before

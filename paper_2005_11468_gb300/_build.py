@@ -10,7 +10,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpsr.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["psr_solve.cu", "mech.cpp"]
+SOURCES = ["psr_solve.cu", "psr_block.cu", "mech.cpp"]
 
 
 def _nvcc():
@@ -33,7 +33,7 @@ def _compile(src, nvcc):
 
 def build(force=False):
     """Compile every translation unit and link libpsr.so; returns the library path."""
-    srcs = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, "psr_internal.h"),
+    srcs = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, "psr_internal.h"), os.path.join(CSRC, "psr_device.cuh"),
                                                          os.path.join(INCLUDE, "psr.h")]
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)

@@ -50,6 +50,71 @@ bool to_i(const std::string &s, long &v) {
     return end && *end == '\0';
 }
 
+// Lagrange weights l_j(p) of the polynomial through nodes 0..nn-1.
+void lagrange(int nn, double p, double *w) {
+    for (int j = 0; j < nn; ++j) {
+        double v = 1.0;
+        for (int k = 0; k < nn; ++k)
+            if (k != j) v *= (p - k) / double(j - k);
+        w[j] = v;
+    }
+}
+
+// MOMIC constants: nucleation, growth prefactor chi_alpha pi d_C^2, coagulation
+// K_f / sqrt(T), moment scales, and the interpolation weights of every fractional
+// moment the sources use (p >= 0: nodes 0..5; p < 0: quadratic over 0, 1, 2).
+int build_soot(Mech &m) {
+    auto get = [&](const char *key, double &v) {
+        for (size_t j = 0; j < m.soot_keys.size(); ++j)
+            if (m.soot_keys[j] == key) {
+                v = m.soot[j];
+                return true;
+            }
+        return false;
+    };
+    double P, H2, nA, nth, cmin, gA, gb, gth, chi, rho_s, eps, m0f;
+    if (!get("precursor", P) || !get("h2", H2) || !get("nuc_A", nA) || !get("nuc_theta", nth) ||
+        !get("cmin", cmin) || !get("grow_A", gA) || !get("grow_beta", gb) || !get("grow_theta", gth) ||
+        !get("chi_alpha", chi) || !get("rho_s", rho_s) || !get("coag_eps", eps) || !get("m0_floor", m0f))
+        return set_error(PSR_E_FORMAT, "psrmech: soot record lacks a constant");
+    if (P < 0 || P >= m.K || H2 < 0 || H2 >= m.K || !(nA > 0) || !(cmin >= 1) || gA < 0 || !(chi >= 0) ||
+        !(rho_s > 0) || eps < 0 || !(m0f > 0))
+        return set_error(PSR_E_FORMAT, "psrmech: soot constant out of range");
+    constexpr double kNA = 6.02214076e23, kKB = 1.380649e-16, kPi = 3.14159265358979323846;
+    const double mC = 12.011 / kNA;
+    const double dC = std::cbrt(6.0 * mC / (kPi * rho_s));
+    std::vector<double> t(kSootLen, 0.0);
+    t[kSootNucLnA] = std::log(nA);
+    t[kSootNucTheta] = nth;
+    t[kSootCmin] = cmin;
+    t[kSootGrowLnA] = gA > 0 ? std::log(gA) : -1e300;
+    t[kSootGrowBeta] = gb;
+    t[kSootGrowTheta] = gth;
+    t[kSootGrowPref] = chi * kPi * dC * dC;
+    t[kSootKf] = eps * std::pow(3.0 * mC / (4.0 * kPi * rho_s), 1.0 / 6.0) * std::sqrt(6.0 * kKB / rho_s);
+    for (int r = 0; r < kNMom; ++r) {
+        t[kSootScale + r] = m0f * std::pow(cmin, r);
+        t[kSootLnScale + r] = std::log(t[kSootScale + r]);
+    }
+    for (int idx = 0; idx < kSootNFrac; ++idx) {
+        double p;
+        if (idx < 24) {
+            const int j = idx / 3, c = idx % 3;
+            p = j + (c == 0 ? 1.0 / 6.0 : (c == 1 ? -1.0 / 6.0 : -0.5));
+        } else {
+            p = (idx - 24) + 2.0 / 3.0;
+        }
+        double *w = t.data() + kSootW + idx * kNMom;
+        if (p >= 0) lagrange(kNMom, p, w);
+        else lagrange(3, p, w);
+    }
+    lagrange(4, 0.5, t.data() + kSootWHalf);
+    m.soot_tab = t;
+    m.soot_P = static_cast<int>(P);
+    m.soot_H2 = static_cast<int>(H2);
+    return PSR_OK;
+}
+
 int parse(const std::string &text, Mech &m) {
     Lines L;
     std::istringstream in(text);
@@ -271,6 +336,10 @@ int parse(const std::string &text, Mech &m) {
             if (kv.second != 0) by_sp[kv.first].push_back({static_cast<int>(i), kv.second});
         }
     }
+    if (m.has_soot) {
+        int rc = build_soot(m);
+        if (rc != PSR_OK) return rc;
+    }
     m.sp_ptr.assign(K + 1, 0);
     for (long k = 0; k < K; ++k) {
         m.sp_ptr[k + 1] = m.sp_ptr[k] + static_cast<int32_t>(by_sp[k].size());
@@ -295,7 +364,7 @@ int upload(Mech &m) {
     std::vector<double> invW(m.K);
     for (int k = 0; k < m.K; ++k) invW[k] = 1.0 / m.W[k];
     size_t oW, oinvW, onasa, olnA, obeta, otheta, oslots, odnu, otype, oeffp, oeffs, oeffv, otr, otroe,
-        osp, ospr, ospn, opart, opartnu, opfm, oprm, oorig, odnud, ospnd;
+        osp, ospr, ospn, opart, opartnu, opfm, oprm, oorig, odnud, ospnd, osoot;
     std::vector<double> dnu_d(m.dnu.begin(), m.dnu.end()), sp_nu_d(m.sp_nu.begin(), m.sp_nu.end());
     place(blob, m.W, oW);
     place(blob, invW, oinvW);
@@ -321,6 +390,7 @@ int upload(Mech &m) {
     place(blob, m.orig, oorig);
     place(blob, dnu_d, odnud);
     place(blob, sp_nu_d, ospnd);
+    place(blob, m.soot_tab, osoot);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_error("cudaGetDevice", e);
@@ -364,6 +434,10 @@ int upload(Mech &m) {
     D.orig = reinterpret_cast<const int32_t *>(b + oorig);
     D.dnu_d = reinterpret_cast<const double *>(b + odnud);
     D.sp_nu_d = reinterpret_cast<const double *>(b + ospnd);
+    D.nsoot = m.has_soot ? kNMom : 0;
+    D.soot_P = m.soot_P;
+    D.soot_H2 = m.soot_H2;
+    D.soot = m.has_soot ? reinterpret_cast<const double *>(b + osoot) : nullptr;
     D.tb_first = m.tb_first;
     D.troe_first = m.troe_first;
     return PSR_OK;
@@ -455,6 +529,7 @@ void psr_options_default(psr_options *o) {
     o->ts_newton = 8;
     o->precision = PSR_FP64;
     o->energy = PSR_ADIABATIC;
+    o->mixed_fallback = 1;
 }
 
 }  // extern "C"

@@ -1,0 +1,1120 @@
+// Batched steady PSR solve for mechanisms too large for one warp (K + 1 > 64): one
+// thread block per reactor, persistent over an atomic work queue.
+//
+// The method and its arithmetic are those of the warp solver: the hybrid damped Newton /
+// pseudo-transient scheme of Sec. 3 on the residual of Eqs. (2)-(3) with the rates of
+// Eqs. (4)-(9). Only the mapping differs. Thread j owns component j (n <= 512); state
+// vectors, species and reaction tables sit in shared memory; the Jacobian [n][P] is in
+// shared memory when it fits (the FP32 Jacobian of a K = 200 mechanism takes 162 KB) and
+// otherwise in a per-block global slot that stays L2-resident (FP64 at K = 200: 323 KB
+// per block, 49 MB for 152 blocks). Block-wide sums use a fixed reduction order, so every
+// thread holds bit-identical scalars and all control flow is block-uniform.
+#include <algorithm>
+#include <string>
+
+#include "psr_device.cuh"
+#include "psr_internal.h"
+
+namespace psr {
+namespace {
+
+constexpr int kBT = 512;          // threads per block
+constexpr int kBW = kBT / 32;     // warps per block
+constexpr int kMaxBlockN = kBT;   // unknowns per reactor: thread j owns component j
+constexpr int kRedSlots = 8;      // values reduced together
+
+// Per-block workspace. Vectors [n]; species [K(+1)]; reactions [I]; Jacobian [n][P].
+template <class TJ>
+struct BWS {
+    double *x, *y, *yt, *c, *F, *R, *Rt, *dy, *db;
+    double *C, *hRT, *gS;     // [K+1] concentrations (C[K] = 1), H/RT, S/R - H/RT (sentinels 0)
+    double *cpR, *dcpR;       // [K] c_p/R and its T-derivative of the last residual
+    double *kf, *kr, *q;      // [I] effective rate constants, q_i (or Euler sums after the Jacobian)
+    double *v, *ra, *rb;      // [K] wdot / dense third-body column part; row coefficients
+    double *tD, *tX;          // [n_troe] falloff derivative caches
+    double *red;              // [kRedSlots][kBW] reduction partials
+    int *ired;                // [kBW] pivot-search partials, then the work-queue slot
+    TJ *J;                    // [n][P]
+    TJ *rhs;                  // [n]
+    int16_t *perm;            // [n]
+    int P;
+};
+
+__host__ __device__ inline int pitch_of(int n) { return (n & 1) ? n : n + 1; }
+
+__host__ __device__ inline size_t bws_doubles(int K, int I, int nt, int n) {
+    return size_t(9) * n + 3 * size_t(K + 1) + 2 * size_t(K) + 3 * size_t(I) + 3 * size_t(K) + 2 * size_t(nt) +
+           size_t(kRedSlots) * kBW;
+}
+
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// Shared-memory bytes of one block: the vector/table part, rhs and perm, and the
+// Jacobian itself when j_in_smem.
+template <class TJ>
+__host__ __device__ inline size_t bws_bytes(int K, int I, int nt, int n, bool j_in_smem) {
+    size_t b = align16(sizeof(double) * bws_doubles(K, I, nt, n));
+    b = align16(b + sizeof(int) * (kBW + 4));
+    b = align16(b + sizeof(TJ) * n);
+    b = align16(b + sizeof(int16_t) * n);
+    if (j_in_smem) b = align16(b + sizeof(TJ) * size_t(n) * pitch_of(n));
+    return b;
+}
+
+template <class TJ>
+__device__ BWS<TJ> bcarve(char *base, int K, int I, int nt, int n, TJ *Jglobal) {
+    BWS<TJ> w;
+    double *d = reinterpret_cast<double *>(base);
+    w.x = d;
+    w.y = d + n;
+    w.yt = d + 2 * n;
+    w.c = d + 3 * n;
+    w.F = d + 4 * n;
+    w.R = d + 5 * n;
+    w.Rt = d + 6 * n;
+    w.dy = d + 7 * n;
+    w.db = d + 8 * n;
+    d += 9 * n;
+    w.C = d;
+    w.hRT = d + (K + 1);
+    w.gS = d + 2 * (K + 1);
+    d += 3 * (K + 1);
+    w.cpR = d;
+    w.dcpR = d + K;
+    d += 2 * K;
+    w.kf = d;
+    w.kr = d + I;
+    w.q = d + 2 * I;
+    d += 3 * I;
+    w.v = d;
+    w.ra = d + K;
+    w.rb = d + 2 * K;
+    d += 3 * K;
+    w.tD = d;
+    w.tX = d + nt;
+    d += 2 * nt;
+    w.red = d;
+    size_t off = align16(sizeof(double) * bws_doubles(K, I, nt, n));
+    w.ired = reinterpret_cast<int *>(base + off);
+    off = align16(off + sizeof(int) * (kBW + 4));
+    w.rhs = reinterpret_cast<TJ *>(base + off);
+    off = align16(off + sizeof(TJ) * n);
+    w.perm = reinterpret_cast<int16_t *>(base + off);
+    off = align16(off + sizeof(int16_t) * n);
+    w.P = pitch_of(n);
+    w.J = Jglobal ? Jglobal : reinterpret_cast<TJ *>(base + off);
+    return w;
+}
+
+// ---------------------------------------------------------------- block reductions
+// Sums of NV values over the block; every thread receives the same totals.
+template <int NV>
+__device__ __forceinline__ void bsum(double (&v)[NV], double *red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = wsum(v[k]);
+    __syncthreads();   // the previous reduction's partials have been read
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[k * kBW + wid] = v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double s = 0.0;
+#pragma unroll
+        for (int u = 0; u < kBW; ++u) s += red[k * kBW + u];
+        v[k] = s;
+    }
+}
+
+__device__ __forceinline__ double bsum1(double x, double *red) {
+    double v[1] = {x};
+    bsum<1>(v, red);
+    return v[0];
+}
+
+__device__ __forceinline__ double bmax(double x, double *red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    x = wmax(x);
+    __syncthreads();
+    if (lane == 0) red[wid] = x;
+    __syncthreads();
+    double m = red[0];
+#pragma unroll
+    for (int u = 1; u < kBW; ++u) m = fmax(m, red[u]);
+    return m;
+}
+
+__device__ __forceinline__ double bmin(double x, double *red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    x = wmin(x);
+    __syncthreads();
+    if (lane == 0) red[wid] = x;
+    __syncthreads();
+    double m = red[0];
+#pragma unroll
+    for (int u = 1; u < kBW; ++u) m = fmin(m, red[u]);
+    return m;
+}
+
+// ---------------------------------------------------------------- residual, Eqs. (2)-(9)
+// F at state y (shared); leaves C, hRT, gS, cpR, dcpR, kf, kr, q, v = wdot and the falloff
+// caches of this state in shared memory and the mixture scalars in mx (every thread).
+template <class TJ>
+__device__ void b_eval_F(const DevMech &M, const BWS<TJ> &w, const double *y, double *F, Mix &mx,
+                         const double *Yin, double tau, double P, double Tspec, int energy,
+                         const double *__restrict__ mult) {
+    const int t = threadIdx.x;
+    const int K = M.K, I = M.I;
+    __syncthreads();   // y complete
+    const double T = y[K];
+    const double lnT = log(T), invT = 1.0 / T;
+    mx.T = T;
+    mx.lnT = lnT;
+    mx.invT = invT;
+    const double sYW = bsum1(t < K ? y[t] * __ldg(M.invW + t) : 0.0, w.red);
+    const double Wbar = 1.0 / sYW;
+    const double rho = P * Wbar / (kRu * T);
+    mx.Wbar = Wbar;
+    mx.rho = rho;
+    mx.Ctot = P / (kRu * T);
+    mx.lnPRT = log(kPatm / (kRu * T));
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // Y_in H/RT/W, Y c_p/R/W, Y_in c_p/R/W, Y dc_p/R/W, H/RT wdot
+    if (t < K) {
+        const double Yj = y[t];
+        double cpR, hRT, sR, dcpR;
+        nasa7(M.nasa, t, T, lnT, invT, cpR, hRT, sR, dcpR);
+        const double invW = __ldg(M.invW + t);
+        w.C[t] = rho * Yj * invW;
+        w.hRT[t] = hRT;
+        w.gS[t] = sR - hRT;
+        w.cpR[t] = cpR;
+        w.dcpR[t] = dcpR;
+        const double yin = Yin[t];
+        acc[0] = yin * hRT * invW;
+        acc[1] = Yj * cpR * invW;
+        acc[2] = yin * cpR * invW;
+        acc[3] = Yj * dcpR * invW;
+    } else if (t == K) {
+        w.C[K] = 1.0;
+        w.hRT[K] = 0.0;
+        w.gS[K] = 0.0;
+    }
+    __syncthreads();
+    // rates of progress, Eqs. (5)-(9): elementary reactions [0, tb_first)
+    const int nE = M.tb_first;
+    for (int i = t; i < nE; i += kBT) {
+        const int16_t *sl6 = M.slots + size_t(i) * 6;
+        const int s0 = __ldg(sl6), s1 = __ldg(sl6 + 1), s2 = __ldg(sl6 + 2), s3 = __ldg(sl6 + 3),
+                  s4 = __ldg(sl6 + 4), s5 = __ldg(sl6 + 5);
+        const double a = __ldg(M.lnA + i) + __ldg(M.beta + i) * lnT - __ldg(M.theta + i) * invT;
+        const double lnKc = (w.gS[s3] + w.gS[s4] + w.gS[s5]) - (w.gS[s0] + w.gS[s1] + w.gS[s2]) +
+                            __ldg(M.dnu_d + i) * mx.lnPRT;
+        const double kf = exp(a), kr = exp(a - lnKc);
+        double q = kf * (w.C[s0] * w.C[s1] * w.C[s2]) - kr * (w.C[s3] * w.C[s4] * w.C[s5]);
+        if (mult) q *= __ldg(mult + __ldg(M.orig + i));
+        w.kf[i] = kf;
+        w.kr[i] = kr;
+        w.q[i] = q;
+    }
+    // third-body and falloff reactions [tb_first, I)
+    for (int i = nE + t; i < I; i += kBT) {
+        const int16_t *sl6 = M.slots + size_t(i) * 6;
+        const int s0 = __ldg(sl6), s1 = __ldg(sl6 + 1), s2 = __ldg(sl6 + 2), s3 = __ldg(sl6 + 3),
+                  s4 = __ldg(sl6 + 4), s5 = __ldg(sl6 + 5);
+        const double a = __ldg(M.lnA + i) + __ldg(M.beta + i) * lnT - __ldg(M.theta + i) * invT;
+        const double lnKc = (w.gS[s3] + w.gS[s4] + w.gS[s5]) - (w.gS[s0] + w.gS[s1] + w.gS[s2]) +
+                            __ldg(M.dnu_d + i) * mx.lnPRT;
+        double kf = exp(a), kr = exp(a - lnKc);
+        const int typ = __ldg(M.type + i);
+        double Mc = mx.Ctot;
+        for (int e = __ldg(M.eff_ptr + i); e < __ldg(M.eff_ptr + i + 1); ++e)
+            Mc += __ldg(M.eff_val + e) * w.C[__ldg(M.eff_sp + e)];
+        if (typ == kTroe) {
+            const int tr = __ldg(M.troe_row + i);
+            Troe tt = troe_eval(M.troe + size_t(tr) * 8, a, Mc, T, lnT, invT, true);
+            kf *= tt.fac;
+            kr *= tt.fac;
+            const double dlkf = __ldg(M.beta + i) * invT + __ldg(M.theta + i) * invT * invT;
+            w.tD[tr] = tt.D;
+            w.tX[tr] = tt.D * (tt.dlk0 - dlkf) + tt.dlnF_dT;
+        }
+        w.kf[i] = kf;
+        w.kr[i] = kr;
+        double q = kf * (w.C[s0] * w.C[s1] * w.C[s2]) - kr * (w.C[s3] * w.C[s4] * w.C[s5]);
+        if (typ == kThirdBody) q *= Mc;
+        if (mult) q *= __ldg(mult + __ldg(M.orig + i));
+        w.q[i] = q;
+    }
+    __syncthreads();
+    // Eq. (4) and the species residuals of Eq. (2); wdot_k is left in v[] for the Jacobian
+    const double tau_rho = tau / rho;
+    if (t < K) {
+        double w0 = 0.0, w1 = 0.0;
+        int e = __ldg(M.sp_ptr + t);
+        const int e_end = __ldg(M.sp_ptr + t + 1);
+        for (; e + 1 < e_end; e += 2) {
+            w0 += __ldg(M.sp_nu_d + e) * w.q[__ldg(M.sp_rxn + e)];
+            w1 += __ldg(M.sp_nu_d + e + 1) * w.q[__ldg(M.sp_rxn + e + 1)];
+        }
+        if (e < e_end) w0 += __ldg(M.sp_nu_d + e) * w.q[__ldg(M.sp_rxn + e)];
+        const double wd = w0 + w1;
+        F[t] = y[t] - Yin[t] - tau_rho * __ldg(M.W + t) * wd;
+        acc[4] = w.hRT[t] * wd;
+        w.v[t] = wd;
+    }
+    bsum<5>(acc, w.red);
+    const double RT = kRu * T;
+    const double cp = acc[1] * kRu;
+    const double N = acc[0] * RT - mx.h_in + tau_rho * RT * acc[4];
+    mx.N = N;
+    mx.cp = cp;
+    mx.sum_yin_cp = acc[2] * kRu;
+    mx.sum_y_dcp = acc[3] * kRu;
+    if (t == K) F[K] = (energy == PSR_FIXED_T) ? (T - Tspec) : N / (cp * T);
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- Jacobian
+// Analytic dF/dx at the state of the last b_eval_F, plus diag(c), into w.J: per-reaction
+// concentration-Jacobian blocks (shared-memory atomics), a dense third-body part per
+// column, Euler sums and T-derivatives per species, the transform to (Y, T) and the
+// energy row of Eq. (3). Same chain and precision as the warp solver's Jacobian.
+template <class TJ>
+__device__ void b_eval_J(const DevMech &M, const BWS<TJ> &w, const double *c, const Mix &mx, double tau,
+                         int energy, const double *__restrict__ mult) {
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int K = M.K, I = M.I, n = K + 1, P = w.P;
+    __syncthreads();
+    const double wd = (t < K) ? w.v[t] : 0.0;
+    __syncthreads();
+    for (size_t idx = t; idx < size_t(n) * P; idx += kBT) w.J[idx] = TJ(0);
+    if (t < K) w.v[t] = 0.0;
+    __syncthreads();
+    const double T = mx.T, invT = mx.invT;
+    for (int i = t; i < I; i += kBT) {
+        const int16_t *sl6 = M.slots + size_t(i) * 6;
+        int s[6];
+        double cs[6];
+#pragma unroll
+        for (int u = 0; u < 6; ++u) {
+            s[u] = __ldg(sl6 + u);
+            cs[u] = w.C[s[u]];
+        }
+        const double Pf = cs[0] * cs[1] * cs[2], Pr_ = cs[3] * cs[4] * cs[5];
+        const double d0 = cs[1] * cs[2], d1 = cs[0] * cs[2], d2 = cs[0] * cs[1];
+        const double d3 = cs[4] * cs[5], d4 = cs[3] * cs[5], d5 = cs[3] * cs[4];
+        const double kf = w.kf[i], kr = w.kr[i];
+        const double m = mult ? __ldg(mult + __ldg(M.orig + i)) : 1.0;
+        const int typ = __ldg(M.type + i);
+        double Mc = 1.0;
+        if (typ != kElem) {
+            Mc = mx.Ctot;
+            for (int e = __ldg(M.eff_ptr + i); e < __ldg(M.eff_ptr + i + 1); ++e)
+                Mc += __ldg(M.eff_val + e) * w.C[__ldg(M.eff_sp + e)];
+        }
+        const double sM = (typ == kThirdBody) ? Mc : 1.0;
+        const double dlkf = __ldg(M.beta + i) * invT + __ldg(M.theta + i) * invT * invT;
+        const double dlKc = ((w.hRT[s[3]] + w.hRT[s[4]] + w.hRT[s[5]]) - (w.hRT[s[0]] + w.hRT[s[1]] + w.hRT[s[2]]) -
+                             __ldg(M.dnu_d + i)) * invT;
+        double dlkfe = dlkf, dqdM = 0.0;
+        if (typ == kThirdBody) {
+            dqdM = m * (kf * Pf - kr * Pr_);
+        } else if (typ == kTroe) {
+            const int tr = __ldg(M.troe_row + i);
+            dlkfe = dlkf + w.tX[tr];
+            dqdM = m * (kf * Pf - kr * Pr_) * w.tD[tr] / Mc;
+        }
+        const double dlkre = dlkfe - dlKc;
+        const double Af = m * sM * kf, Ar = m * sM * kr;
+        const int nf = (s[0] < K) + (s[1] < K) + (s[2] < K), nr = (s[3] < K) + (s[4] < K) + (s[5] < K);
+        double g = Af * nf * Pf - Ar * nr * Pr_;
+        if (typ != kElem) g += dqdM * Mc;
+        const double dqdT = Af * Pf * dlkfe - Ar * Pr_ * dlkre;
+        const int16_t *pp = M.part + size_t(i) * 6;
+        const int8_t *pn = M.part_nu + size_t(i) * 6;
+        const int8_t *pfm = M.part_fm + size_t(i) * 6;
+        const int8_t *prm = M.part_rm + size_t(i) * 6;
+        int pl[6];
+        TJ pnu[6], val[6];
+#pragma unroll
+        for (int u = 0; u < 6; ++u) {
+            pl[u] = __ldg(pp + u);
+            pnu[u] = TJ(__ldg(pn + u));
+            const int fm = __ldg(pfm + u), rm = __ldg(prm + u);
+            const double dfl = ((fm & 1) ? d0 : 0.0) + ((fm & 2) ? d1 : 0.0) + ((fm & 4) ? d2 : 0.0);
+            const double drl = ((rm & 1) ? d3 : 0.0) + ((rm & 2) ? d4 : 0.0) + ((rm & 4) ? d5 : 0.0);
+            val[u] = TJ(Af * dfl - Ar * drl);
+        }
+        const TJ dqdM_t = TJ(dqdM);
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+            if (pl[r] >= K || pnu[r] == TJ(0)) continue;
+            TJ *row = w.J + size_t(pl[r]) * P;
+#pragma unroll
+            for (int u = 0; u < 6; ++u) {
+                if (pl[u] >= K) continue;
+                atomicAdd(row + pl[u], pnu[r] * val[u]);
+            }
+            if (typ != kElem) {
+                atomicAdd(w.v + pl[r], double(pnu[r]) * dqdM);
+                for (int e = __ldg(M.eff_ptr + i); e < __ldg(M.eff_ptr + i + 1); ++e)
+                    atomicAdd(row + __ldg(M.eff_sp + e), pnu[r] * dqdM_t * TJ(__ldg(M.eff_val + e)));
+            }
+        }
+        w.q[i] = g;       // per-reaction Euler sum
+        w.kf[i] = dqdT;   // and T-derivative replace q and kf
+    }
+    __syncthreads();
+    double sk = 0.0, wT = 0.0, vk = 0.0;
+    if (t < K) {
+        for (int e = __ldg(M.sp_ptr + t); e < __ldg(M.sp_ptr + t + 1); ++e) {
+            const double nu = __ldg(M.sp_nu_d + e);
+            const int r = __ldg(M.sp_rxn + e);
+            sk += nu * w.q[r];
+            wT += nu * w.kf[r];
+        }
+        vk = w.v[t];
+    }
+    const double rho = mx.rho, Wbar = mx.Wbar, RT = kRu * T;
+    double eJ = 0.0;
+    if (energy != PSR_FIXED_T) {
+        double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // Q, Sh, Hv, cw, hwT
+        if (t < K) {
+            const double H = w.hRT[t] * RT;
+            acc[0] = H * wd;
+            acc[1] = H * sk;
+            acc[2] = H * vk;
+            acc[3] = w.cpR[t] * kRu * wd;
+            acc[4] = H * (wT - sk * invT);
+        }
+        bsum<5>(acc, w.red);
+        const double Q = acc[0], Sh = acc[1], Hv = acc[2], cw = acc[3], hwT = acc[4];
+        const double N = mx.N, cp = mx.cp;
+        const double inv_cpT = 1.0 / (cp * T);
+        if (t < K) {
+            TJ colsum = TJ(0);
+            for (int k = 0; k < K; ++k) colsum += TJ(w.hRT[k]) * w.J[size_t(k) * P + t];
+            const double cs = double(colsum) * RT + Hv;
+            const double invWj = __ldg(M.invW + t);
+            const double dN = tau * invWj * (cs + Wbar * (Q - Sh) / rho);
+            const double cpj = w.cpR[t] * kRu * invWj;
+            eJ = dN * inv_cpT - N * cpj * inv_cpT / cp;
+        } else if (t == K) {
+            const double dNdT = mx.sum_yin_cp + tau / rho * (cw + hwT) + tau * Q / (rho * T);
+            eJ = dNdT * inv_cpT - N * mx.sum_y_dcp * inv_cpT / cp - N * inv_cpT * invT;
+        }
+    }
+    if (t < K) {
+        const double Wk = __ldg(M.W + t);
+        w.ra[t] = tau * Wk;
+        w.rb[t] = tau * Wk * Wbar * (sk - wd) / rho;
+        // column K (untouched by the reaction pass) of species row t
+        w.J[size_t(t) * P + K] = TJ(-(tau * Wk / rho) * (wT + (wd - sk) * invT));
+    }
+    __syncthreads();   // column sums read J before the transform rewrites it
+    // species rows: dF_k/dY_j = delta_kj - tau W_k (Jc_kj + v_k)/W_j + tau W_k Wbar (s_k - wdot_k)/(rho W_j)
+    for (int k = wid; k < K; k += kBW) {
+        const TJ ak = TJ(w.ra[k]), bk = TJ(w.rb[k]), vkt = TJ(w.v[k]);
+        TJ *row = w.J + size_t(k) * P;
+        for (int j = lane; j < K; j += 32) {
+            const TJ invWj = TJ(__ldg(M.invW + j));
+            row[j] = (bk - ak * (row[j] + vkt)) * invWj + ((j == k) ? TJ(1) : TJ(0));
+        }
+    }
+    if (t < n) {
+        const double v = (energy == PSR_FIXED_T) ? ((t == K) ? 1.0 : 0.0) : eJ;
+        w.J[size_t(K) * P + t] = TJ(v);
+    }
+    __syncthreads();
+    if (t < n) w.J[size_t(t) * P + t] = TJ(double(w.J[size_t(t) * P + t]) + c[t]);
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- LU (partial pivoting)
+// In-place LU of w.J with row interchanges (perm = final row order); rows below the pivot
+// are updated one warp per row, lanes over columns. False on a zero or non-finite pivot
+// (block-uniform).
+template <class TJ>
+__device__ bool b_lu_factor(const BWS<TJ> &w, int n) {
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int P = w.P;
+    if (t < n) w.perm[t] = int16_t(t);
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        // pivot: first row of largest |a_ik|, i >= k (thread t inspects row k + t)
+        double best = -1.0;
+        int bi = n;
+        {
+            const int i = k + t;
+            if (i < n) {
+                double a = fabs(double(w.J[size_t(i) * P + k]));
+                if (a != a) a = INFINITY;   // a NaN candidate fails the factorisation below
+                best = a;
+                bi = i;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(kFull, best, o);
+            const int oi = __shfl_xor_sync(kFull, bi, o);
+            if (ob > best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            w.red[wid] = best;
+            w.ired[wid] = bi;
+        }
+        __syncthreads();
+        best = w.red[0];
+        bi = w.ired[0];
+#pragma unroll
+        for (int u = 1; u < kBW; ++u) {
+            const double ob = w.red[u];
+            const int oi = w.ired[u];
+            if (ob > best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        const int p = bi;
+        const double pv = (p < n) ? double(w.J[size_t(p) * P + k]) : 0.0;
+        __syncthreads();   // partials and the pivot are read before anything overwrites them
+        if (!(pv != 0.0) || !isfinite(pv)) return false;
+        if (p != k) {
+            for (int j = t; j < n; j += kBT) {
+                const TJ tmp = w.J[size_t(k) * P + j];
+                w.J[size_t(k) * P + j] = w.J[size_t(p) * P + j];
+                w.J[size_t(p) * P + j] = tmp;
+            }
+            if (t == 0) {
+                const int16_t tp = w.perm[k];
+                w.perm[k] = w.perm[p];
+                w.perm[p] = tp;
+            }
+            __syncthreads();
+        }
+        const TJ inv = TJ(1.0) / TJ(pv);
+        const TJ *rk = w.J + size_t(k) * P;
+        for (int r = k + 1 + wid; r < n; r += kBW) {
+            TJ *ri = w.J + size_t(r) * P;
+            const TJ l = ri[k] * inv;
+            for (int j = k + 1 + lane; j < n; j += 32) ri[j] = fma(-l, rk[j], ri[j]);
+            __syncwarp();   // every lane has read ri[k]
+            if (lane == 0) ri[k] = l;
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+// x = -(LU)^-1 r (r, x shared vectors of length n); the substitutions run on warp 0.
+template <class TJ>
+__device__ void b_lu_solve_neg(const BWS<TJ> &w, int n, const double *r, double *x) {
+    const int t = threadIdx.x;
+    const int P = w.P;
+    __syncthreads();   // r complete
+    if (t < n) w.rhs[t] = TJ(-r[w.perm[t]]);
+    __syncthreads();
+    if (t < 32) {
+        const int lane = t;
+        for (int k = 0; k < n - 1; ++k) {
+            const TJ bk = w.rhs[k];
+            for (int i = k + 1 + lane; i < n; i += 32) w.rhs[i] = fma(-w.J[size_t(i) * P + k], bk, w.rhs[i]);
+            __syncwarp();
+        }
+        for (int k = n - 1; k >= 0; --k) {
+            const TJ xk = w.rhs[k] / w.J[size_t(k) * P + k];
+            __syncwarp();
+            for (int i = lane; i < k; i += 32) w.rhs[i] = fma(-w.J[size_t(i) * P + k], xk, w.rhs[i]);
+            if (lane == 0) w.rhs[k] = xk;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    if (t < n) x[t] = double(w.rhs[t]);
+    __syncthreads();
+}
+
+// J^T lam = g with the factors of P J = L U (U^T forward, L^T backward, lam[perm[j]] = v_j).
+template <class TJ>
+__device__ void b_lu_solve_T(const BWS<TJ> &w, int n, const double *g, double *lam) {
+    const int t = threadIdx.x;
+    const int P = w.P;
+    __syncthreads();
+    if (t < n) w.rhs[t] = TJ(g[t]);
+    __syncthreads();
+    if (t < 32) {
+        const int lane = t;
+        for (int k = 0; k < n; ++k) {
+            const TJ zk = w.rhs[k] / w.J[size_t(k) * P + k];
+            __syncwarp();
+            for (int j = k + 1 + lane; j < n; j += 32) w.rhs[j] = fma(-w.J[size_t(k) * P + j], zk, w.rhs[j]);
+            if (lane == 0) w.rhs[k] = zk;
+            __syncwarp();
+        }
+        for (int k = n - 1; k >= 1; --k) {
+            const TJ vk = w.rhs[k];
+            for (int j = lane; j < k; j += 32) w.rhs[j] = fma(-w.J[size_t(k) * P + j], vk, w.rhs[j]);
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    if (t < n) lam[w.perm[t]] = double(w.rhs[t]);
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- solver pieces
+struct BCtx {
+    DevMech M;
+    Opts o;
+    const double *Yin;
+    double tau, P, Tspec;
+    const double *mult;
+    int nfev;
+    Mix mx;
+    int K, n;
+};
+
+__device__ __forceinline__ bool b_all_finite(const double *v, int n) {
+    const int t = threadIdx.x;
+    return __syncthreads_and(t >= n || isfinite(v[t])) != 0;
+}
+
+// mass fractions absolute, temperature relative
+__device__ __forceinline__ double b_scaled_max(const double *dy, const double *y, int K, int n, double *red) {
+    const int t = threadIdx.x;
+    double d = 0.0;
+    if (t < n) {
+        d = fabs(dy[t]);
+        if (t == K) d /= fabs(y[t]);
+    }
+    return bmax(d, red);
+}
+
+__device__ __forceinline__ bool b_in_bounds(const double *y, int K, const Opts &o) {
+    const int t = threadIdx.x;
+    bool ok = true;
+    if (t < K) ok = y[t] >= -o.y_floor;
+    else if (t == K) ok = y[t] >= o.t_min && y[t] <= o.t_max;
+    return __syncthreads_and(ok) != 0;
+}
+
+__device__ __forceinline__ double b_max_in_bounds(const double *y, const double *dy, int K, const Opts &o,
+                                                  double *red) {
+    const int t = threadIdx.x;
+    double lam = INFINITY;
+    if (t <= K) {
+        const double x = y[t], d = dy[t];
+        const double lo = (t < K) ? -o.y_floor : o.t_min, hi = (t < K) ? INFINITY : o.t_max;
+        if (d < 0 && x + d < lo) lam = (lo - x) / d;
+        else if (d > 0 && x + d > hi) lam = (hi - x) / d;
+    }
+    return bmin(lam, red);
+}
+
+// |dx_j| <= rtol |x_j| + atol_j (atol_y for species, atol_t for temperature)
+__device__ __forceinline__ bool b_step_small(const double *dy, const double *y, int K, int n, double rtol,
+                                             double atol_y, double atol_t) {
+    const int t = threadIdx.x;
+    bool ok = true;
+    if (t < n) ok = fabs(dy[t]) <= rtol * fabs(y[t]) + ((t < K) ? atol_y : atol_t);
+    return __syncthreads_and(ok) != 0;
+}
+
+template <class TJ>
+__device__ void b_residual_R(BCtx &cx, const BWS<TJ> &w, const double *y, const double *c, const double *xref,
+                             double *F, double *R) {
+    ++cx.nfev;
+    b_eval_F(cx.M, w, y, F, cx.mx, cx.Yin, cx.tau, cx.P, cx.Tspec, cx.o.energy, cx.mult);
+    const int t = threadIdx.x;
+    if (t < cx.n) R[t] = F[t] + c[t] * (y[t] - xref[t]);
+    __syncthreads();
+}
+
+// Damped Newton on R(y) = F(y) + c (y - xref) from y (y updated in place), the scheme of
+// the warp solver: natural-monotonicity damping with the same LU factors, divergence
+// stop, bounds; steady mode converges on ||R||_inf <= ftol plus a small last step.
+template <class TJ>
+__device__ bool b_damped_newton(BCtx &cx, const BWS<TJ> &w, double *y, const double *xref, const double *c,
+                                int max_it, bool steady, int &counter) {
+    const int t = threadIdx.x;
+    const int K = cx.K, n = cx.n;
+    const Opts &o = cx.o;
+    b_residual_R(cx, w, y, c, xref, w.F, w.R);
+    double dn_prev = INFINITY;
+    for (int it = 0; it < max_it; ++it) {
+        if (counter >= o.max_newton) break;
+        ++counter;
+        b_eval_J(cx.M, w, c, cx.mx, cx.tau, o.energy, cx.mult);
+        if (!b_lu_factor(w, n)) break;
+        b_lu_solve_neg(w, n, w.R, w.dy);
+        if (!b_all_finite(w.dy, n)) break;
+        bool done;
+        if (steady) {
+            const double rmax = bmax(t < n ? fabs(w.R[t]) : 0.0, w.red);
+            done = rmax <= o.ftol && b_step_small(w.dy, y, K, n, o.step_rtol, o.step_atol_y, o.step_atol_t);
+        } else {
+            done = b_step_small(w.dy, y, K, n, o.ts_rtol, o.ts_atol_y, o.ts_rtol);
+        }
+        if (done) {
+            if (t < n) y[t] += w.dy[t];
+            __syncthreads();
+            return true;
+        }
+        const double dn = b_scaled_max(w.dy, y, K, n, w.red);
+        if (dn >= dn_prev) break;
+        dn_prev = dn;
+        double lam = fmin(1.0, b_max_in_bounds(y, w.dy, K, o, w.red));
+        bool accepted = false;
+        for (int d = 0; d < o.max_damp; ++d) {
+            if (t < n) w.yt[t] = y[t] + lam * w.dy[t];
+            __syncthreads();
+            if (b_in_bounds(w.yt, K, o)) {
+                b_residual_R(cx, w, w.yt, c, xref, w.F, w.Rt);
+                if (b_all_finite(w.Rt, n)) {
+                    b_lu_solve_neg(w, n, w.Rt, w.db);
+                    if (b_scaled_max(w.db, y, K, n, w.red) < dn) {
+                        accepted = true;
+                        break;
+                    }
+                }
+            }
+            lam *= 0.5;
+        }
+        if (!accepted) break;
+        if (t < n) {
+            y[t] = w.yt[t];
+            w.R[t] = w.Rt[t];
+        }
+        __syncthreads();
+    }
+    return false;
+}
+
+__device__ void b_inlet_enthalpy(BCtx &cx, double Tin, double *red) {
+    const int t = threadIdx.x;
+    const double lnTin = log(Tin);
+    double s = 0.0;
+    if (t < cx.K) {
+        double cpR, hRT, sR, dcpR;
+        nasa7(cx.M.nasa, t, Tin, lnTin, 1.0 / Tin, cpR, hRT, sR, dcpR);
+        s = cx.Yin[t] * hRT * __ldg(cx.M.invW + t);
+    }
+    cx.mx.h_in = bsum1(s, red) * kRu * Tin;
+}
+
+template <class TJ>
+__device__ void b_load_reactor(BCtx &cx, const BWS<TJ> &w, const Batch &bt, int64_t r) {
+    const int t = threadIdx.x;
+    const int K = cx.K;
+    cx.Yin = bt.Y_in + r * K;
+    cx.tau = bt.tau[r];
+    cx.P = bt.P[r];
+    cx.Tspec = bt.T0[r];
+    cx.nfev = 0;
+    b_inlet_enthalpy(cx, bt.T_in[r], w.red);
+    if (t < cx.n) {
+        w.x[t] = (t < K) ? bt.Y0[r * K + t] : bt.T0[r];
+        w.c[t] = 0.0;
+    }
+    __syncthreads();
+}
+
+template <class TJ>
+__device__ void b_solve_one(BCtx &cx, const BWS<TJ> &w, const Batch &bt, int64_t r) {
+    const int t = threadIdx.x;
+    const int K = cx.K, n = cx.n;
+    const Opts &o = cx.o;
+    b_load_reactor(cx, w, bt, r);
+    const double tau = cx.tau;
+    b_residual_R(cx, w, w.x, w.c, w.x, w.F, w.R);
+    int status, counter = 0, ts = 0, rounds = 0;
+    const double *out = w.x;
+    if (!b_all_finite(w.F, n)) {
+        status = PSR_NONFINITE;
+    } else {
+        double dt = o.dt0_over_tau * tau;
+        while (true) {
+            if (t < n) {
+                w.y[t] = w.x[t];
+                w.c[t] = 0.0;
+            }
+            __syncthreads();
+            const bool conv = b_damped_newton(cx, w, w.y, w.x, w.c, o.max_newton, true, counter);
+            if (conv) {
+                status = PSR_CONVERGED;
+                out = w.y;
+                break;
+            }
+            if (counter >= o.max_newton) {
+                status = PSR_MAX_ITER;
+                out = w.y;
+                break;
+            }
+            ++rounds;
+            if (rounds > o.max_ts_rounds) {
+                status = PSR_TS_EXHAUSTED;
+                out = w.x;
+                break;
+            }
+            int taken = 0;
+            bool done = false;
+            while (taken < o.ts_steps) {
+                const double Tx = w.x[K];
+                const double s = tau / dt;
+                const double sT = (o.energy == PSR_FIXED_T) ? s : s / Tx;
+                __syncthreads();   // every thread has read x[K]
+                if (t < n) {
+                    w.c[t] = (t < K) ? s : sT;
+                    w.y[t] = w.x[t];
+                }
+                __syncthreads();
+                const int used0 = counter;
+                const bool ok = b_damped_newton(cx, w, w.y, w.x, w.c, o.ts_newton, false, counter);
+                const int used = counter - used0;
+                if (counter >= o.max_newton) {
+                    status = PSR_MAX_ITER;
+                    out = w.x;
+                    done = true;
+                    break;
+                }
+                if (ok) {
+                    if (t < n) w.x[t] = w.y[t];
+                    __syncthreads();
+                    ++taken;
+                    ++ts;
+                    const double g = (used <= 3) ? 2.0 : (used == 4 ? 1.25 : 1.0);
+                    dt = fmin(g * dt, 1e6 * tau);
+                } else {
+                    dt *= o.dt_shrink;
+                    if (dt < 1e-16 * tau) {
+                        status = PSR_TS_EXHAUSTED;
+                        out = w.x;
+                        done = true;
+                        break;
+                    }
+                }
+            }
+            if (done) break;
+        }
+    }
+    // report ||F||_inf at the output state
+    if (t < n) w.c[t] = 0.0;
+    __syncthreads();
+    b_residual_R(cx, w, out, w.c, out, w.F, w.R);
+    const double fn = bmax(t < n ? fabs(w.F[t]) : 0.0, w.red);
+    if (t < K) bt.Y_out[r * K + t] = out[t];
+    if (t == 0) {
+        bt.T_out[r] = out[K];
+        const bool fb = bt.fallback != 0;
+        if (bt.status) bt.status[r] = (fb && status == PSR_CONVERGED) ? PSR_REFINE_FALLBACK : status;
+        if (bt.iters) bt.iters[r] = counter + (fb ? bt.iters[r] : 0);
+        if (bt.ts_steps) bt.ts_steps[r] = ts + (fb ? bt.ts_steps[r] : 0);
+        if (bt.fnorm) bt.fnorm[r] = fn;
+        if (bt.nfev) bt.nfev[r] = cx.nfev + (fb ? bt.nfev[r] : 0);
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- kernels
+template <class TJ>
+__global__ void __launch_bounds__(kBT, 1) block_solve_kernel(DevMech M, Batch bt, Opts o, int *queue, TJ *Jglob) {
+    extern __shared__ __align__(16) char smem[];
+    const int K = M.K, n = K + 1;
+    const size_t slot = size_t(n) * pitch_of(n);
+    BWS<TJ> w = bcarve<TJ>(smem, K, M.I, M.n_troe, n, Jglob ? Jglob + blockIdx.x * slot : nullptr);
+    BCtx cx;
+    cx.M = M;
+    cx.o = o;
+    cx.mult = bt.rate_mult;
+    cx.K = K;
+    cx.n = n;
+    const int64_t nwork = bt.list ? int64_t(*bt.list_len) : bt.B;
+    while (true) {
+        if (threadIdx.x == 0) w.ired[kBW] = atomicAdd(queue, 1);
+        __syncthreads();
+        const int p = w.ired[kBW];
+        __syncthreads();
+        if (p >= nwork) break;
+        const int64_t r = bt.list ? int64_t(bt.list[p]) : int64_t(p);
+        b_solve_one<TJ>(cx, w, bt, r);
+    }
+}
+
+__global__ void block_collect_unconverged(int64_t B, const int32_t *status, int32_t *list, int32_t *len) {
+    const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (r < B && status[r] != PSR_CONVERGED) list[atomicAdd(len, 1)] = int32_t(r);
+}
+
+// residual or Jacobian at given states, one block per state (grid-stride over states)
+template <class TJ>
+__global__ void __launch_bounds__(kBT, 1) block_eval_kernel(DevMech M, Batch bt, int energy, int want_J,
+                                                            double *out, TJ *Jglob) {
+    extern __shared__ __align__(16) char smem[];
+    const int K = M.K, n = K + 1;
+    const size_t slot = size_t(n) * pitch_of(n);
+    BWS<TJ> w = bcarve<TJ>(smem, K, M.I, M.n_troe, n, Jglob ? Jglob + blockIdx.x * slot : nullptr);
+    BCtx cx;
+    cx.M = M;
+    cx.o.energy = energy;
+    cx.mult = bt.rate_mult;
+    cx.K = K;
+    cx.n = n;
+    const int t = threadIdx.x;
+    for (int64_t r = blockIdx.x; r < bt.B; r += gridDim.x) {
+        b_load_reactor(cx, w, bt, r);
+        b_residual_R(cx, w, w.x, w.c, w.x, w.F, w.R);
+        if (!want_J) {
+            if (t < n) out[r * n + t] = w.F[t];
+            continue;
+        }
+        b_eval_J(M, w, w.c, cx.mx, cx.tau, energy, cx.mult);
+        for (int idx = t; idx < n * n; idx += kBT)
+            out[r * n * n + idx] = double(w.J[size_t(idx / n) * w.P + idx % n]);
+        __syncthreads();
+    }
+}
+
+// Adjoint sensitivities at given (converged) states (the warp solver's formula):
+// J^T lam = g with the FP64 factors, then
+// dL/d ln m_i = (tau q_i / rho) [sum_k lam_k W_k nu_ki - lam_T dH_i / (c_p T)].
+__global__ void __launch_bounds__(kBT, 1) block_adjoint_kernel(DevMech M, Batch bt, int energy, const double *g,
+                                                               double *grad, double *lam_out, int32_t *ok,
+                                                               double *Jglob) {
+    extern __shared__ __align__(16) char smem[];
+    const int K = M.K, n = K + 1, I = M.I;
+    const size_t slot = size_t(n) * pitch_of(n);
+    BWS<double> w = bcarve<double>(smem, K, I, M.n_troe, n, Jglob ? Jglob + blockIdx.x * slot : nullptr);
+    BCtx cx;
+    cx.M = M;
+    cx.o.energy = energy;
+    cx.mult = bt.rate_mult;
+    cx.K = K;
+    cx.n = n;
+    const int t = threadIdx.x;
+    for (int64_t r = blockIdx.x; r < bt.B; r += gridDim.x) {
+        b_load_reactor(cx, w, bt, r);
+        b_residual_R(cx, w, w.x, w.c, w.x, w.F, w.R);
+        b_eval_J(M, w, w.c, cx.mx, cx.tau, energy, cx.mult);
+        const bool good = b_lu_factor(w, n);
+        if (t < n) {
+            w.dy[t] = 0.0;
+            w.db[t] = g[r * n + t];
+        }
+        __syncthreads();
+        if (good) b_lu_solve_T(w, n, w.db, w.dy);   // lam in dy
+        // the Jacobian pass replaced q_i: evaluate the residual once more to restore it
+        b_residual_R(cx, w, w.x, w.c, w.x, w.F, w.R);
+        if (lam_out && t < n) lam_out[r * n + t] = w.dy[t];
+        const double lamT = w.dy[K];
+        if (t < K) w.v[t] = w.dy[t] * __ldg(M.W + t);
+        __syncthreads();
+        const double tau_rho = cx.tau / cx.mx.rho;
+        const double eT = (energy == PSR_FIXED_T) ? 0.0 : lamT * kRu * cx.mx.T / (cx.mx.cp * cx.mx.T);
+        for (int i = t; i < I; i += kBT) {
+            const int16_t *pp = M.part + size_t(i) * 6;
+            const int8_t *pn = M.part_nu + size_t(i) * 6;
+            double lw = 0.0, dH = 0.0;
+            for (int u = 0; u < 6; ++u) {
+                const int l = __ldg(pp + u);
+                if (l >= K) continue;
+                const double nu = double(__ldg(pn + u));
+                lw += nu * w.v[l];
+                dH += nu * w.hRT[l];
+            }
+            grad[r * I + __ldg(M.orig + i)] = good ? tau_rho * w.q[i] * (lw - eT * dH) : 0.0;
+        }
+        if (ok && t == 0) ok[r] = good ? 1 : 0;
+        __syncthreads();
+    }
+}
+
+template <class TJ>
+__global__ void __launch_bounds__(kBT, 1) block_lu_kernel(int64_t B, int n, const double *A, const double *rhs,
+                                                          double *x, int32_t *ok, TJ *Jglob) {
+    extern __shared__ __align__(16) char smem[];
+    const size_t slot = size_t(n) * pitch_of(n);
+    BWS<TJ> w = bcarve<TJ>(smem, 0, 0, 0, n, Jglob ? Jglob + blockIdx.x * slot : nullptr);
+    const int t = threadIdx.x;
+    for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
+        for (int idx = t; idx < n * n; idx += kBT) w.J[size_t(idx / n) * w.P + idx % n] = TJ(A[b * n * n + idx]);
+        if (t < n) w.R[t] = -rhs[b * n + t];
+        __syncthreads();
+        const bool good = b_lu_factor(w, n);
+        if (good) b_lu_solve_neg(w, n, w.R, w.dy);
+        if (t < n) x[b * n + t] = good ? w.dy[t] : 0.0;
+        if (t == 0) ok[b] = good ? 1 : 0;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- host side
+struct Launch {
+    size_t smem = 0;
+    bool j_in_smem = false;
+    int grid = 0;
+};
+
+// Shared-memory plan of one block for a kernel: the Jacobian in shared memory when the
+// whole workspace fits, else in global slots (one per block).
+template <class TJ, class KernelT>
+int plan(KernelT kern, int K, int I, int nt, int n, int64_t units, int bps_req, Launch &L) {
+    int dev = 0, max_smem = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const size_t with_j = bws_bytes<TJ>(K, I, nt, n, true);
+    L.j_in_smem = with_j <= size_t(max_smem);
+    L.smem = L.j_in_smem ? with_j : bws_bytes<TJ>(K, I, nt, n, false);
+    if (L.smem > size_t(max_smem))
+        return set_error(PSR_E_UNSUPPORTED, "mechanism tables exceed one block's shared memory");
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L.smem));
+    if (e != cudaSuccess) return cuda_error("cudaFuncSetAttribute", e);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBT, L.smem);
+    if (e != cudaSuccess) return cuda_error("occupancy", e);
+    if (per_sm < 1) return set_error(PSR_E_UNSUPPORTED, "block solver kernel does not fit on an SM");
+    if (bps_req > 0 && bps_req < per_sm) per_sm = bps_req;
+    L.grid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(per_sm) * nsm, units)));
+    return PSR_OK;
+}
+
+template <class TJ>
+int launch_block(const Mech &m, const Batch &bt, const Opts &o, int bps_req, cudaStream_t st, int *queue) {
+    const int K = m.K, n = K + 1;
+    Launch L;
+    int rc = plan<TJ>(block_solve_kernel<TJ>, K, m.I, m.n_troe, n, bt.B, bps_req, L);
+    if (rc) return rc;
+    TJ *Jg = nullptr;
+    cudaError_t e;
+    if (!L.j_in_smem) {
+        e = cudaMallocAsync(reinterpret_cast<void **>(&Jg), sizeof(TJ) * size_t(n) * pitch_of(n) * L.grid, st);
+        if (e != cudaSuccess) return set_error(PSR_E_OOM, "Jacobian slots for the block solver");
+    }
+    e = cudaMemsetAsync(queue, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+        block_solve_kernel<TJ><<<L.grid, kBT, L.smem, st>>>(m.dev, bt, o, queue, Jg);
+        e = cudaGetLastError();
+    }
+    if (Jg) cudaFreeAsync(Jg, st);
+    if (e != cudaSuccess) return cuda_error("block_solve_kernel launch", e);
+    return PSR_OK;
+}
+
+}  // namespace
+
+int block_check(const Mech &m) {
+    if (m.dev.nsoot) return set_error(PSR_E_UNSUPPORTED, "soot moments need K + 7 <= 64 (warp solver)");
+    if (m.K + 1 > kMaxBlockN) return set_error(PSR_E_UNSUPPORTED, "the block solver handles at most 512 unknowns");
+    return PSR_OK;
+}
+
+int block_solve(const Mech &m, const Batch &bt, const Opts &o, int precision, bool fallback, int bps_req,
+                cudaStream_t st) {
+    const size_t B = size_t(bt.B);
+    const bool mixed = precision == PSR_MIXED;
+    const size_t n_ints = 4 + ((mixed && fallback) ? B + (bt.status ? 0 : B) : 0);
+    int32_t *scr = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scr), n_ints * sizeof(int32_t), st);
+    if (e != cudaSuccess) return set_error(PSR_E_OOM, "scratch allocation failed");
+    int rc;
+    if (!mixed) {
+        rc = launch_block<double>(m, bt, o, bps_req, st, scr);
+    } else if (!fallback) {
+        rc = launch_block<float>(m, bt, o, bps_req, st, scr);
+    } else {
+        // FP32-Jacobian launch, then the reactors it left unconverged again in FP64
+        int32_t *len = scr + 2, *list = scr + 4;
+        Batch b1 = bt;
+        if (!bt.status) b1.status = scr + 4 + B;
+        rc = launch_block<float>(m, b1, o, bps_req, st, scr);
+        if (rc == PSR_OK) {
+            cudaMemsetAsync(len, 0, sizeof(int32_t), st);
+            block_collect_unconverged<<<unsigned((B + 255) / 256), 256, 0, st>>>(bt.B, b1.status, list, len);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) rc = cuda_error("block_collect_unconverged launch", e);
+        }
+        if (rc == PSR_OK) {
+            Batch b2 = b1;
+            b2.list = list;
+            b2.list_len = len;
+            b2.fallback = 1;
+            rc = launch_block<double>(m, b2, o, bps_req, st, scr + 1);
+        }
+    }
+    cudaFreeAsync(scr, st);
+    return rc;
+}
+
+template <class TJ>
+static int block_eval_t(const Mech &m, const Batch &bt, int energy, int want_J, double *out, cudaStream_t st) {
+    const int K = m.K, n = K + 1;
+    Launch L;
+    int rc = plan<TJ>(block_eval_kernel<TJ>, K, m.I, m.n_troe, n, bt.B, 0, L);
+    if (rc) return rc;
+    TJ *Jg = nullptr;
+    cudaError_t e;
+    if (!L.j_in_smem) {
+        e = cudaMallocAsync(reinterpret_cast<void **>(&Jg), sizeof(TJ) * size_t(n) * pitch_of(n) * L.grid, st);
+        if (e != cudaSuccess) return set_error(PSR_E_OOM, "Jacobian slots for the block evaluator");
+    }
+    block_eval_kernel<TJ><<<L.grid, kBT, L.smem, st>>>(m.dev, bt, energy, want_J, out, Jg);
+    e = cudaGetLastError();
+    if (Jg) cudaFreeAsync(Jg, st);
+    if (e != cudaSuccess) return cuda_error("block_eval_kernel launch", e);
+    return PSR_OK;
+}
+
+int block_eval(const Mech &m, const Batch &bt, int energy, int want_J, int precision, double *out, cudaStream_t st) {
+    if (precision == PSR_MIXED && want_J) return block_eval_t<float>(m, bt, energy, want_J, out, st);
+    return block_eval_t<double>(m, bt, energy, want_J, out, st);
+}
+
+int block_adjoint(const Mech &m, const Batch &bt, int energy, const double *g, double *grad, double *lam_out,
+                  int32_t *ok, cudaStream_t st) {
+    const int K = m.K, n = K + 1;
+    Launch L;
+    int rc = plan<double>(block_adjoint_kernel, K, m.I, m.n_troe, n, bt.B, 0, L);
+    if (rc) return rc;
+    double *Jg = nullptr;
+    cudaError_t e;
+    if (!L.j_in_smem) {
+        e = cudaMallocAsync(reinterpret_cast<void **>(&Jg), sizeof(double) * size_t(n) * pitch_of(n) * L.grid, st);
+        if (e != cudaSuccess) return set_error(PSR_E_OOM, "Jacobian slots for the block adjoint");
+    }
+    block_adjoint_kernel<<<L.grid, kBT, L.smem, st>>>(m.dev, bt, energy, g, grad, lam_out, ok, Jg);
+    e = cudaGetLastError();
+    if (Jg) cudaFreeAsync(Jg, st);
+    if (e != cudaSuccess) return cuda_error("block_adjoint_kernel launch", e);
+    return PSR_OK;
+}
+
+template <class TJ>
+static int block_lu_t(int64_t B, int n, const double *A, const double *r, double *x, int32_t *ok, cudaStream_t st) {
+    Launch L;
+    int rc = plan<TJ>(block_lu_kernel<TJ>, 0, 0, 0, n, B, 0, L);
+    if (rc) return rc;
+    TJ *Jg = nullptr;
+    cudaError_t e;
+    if (!L.j_in_smem) {
+        e = cudaMallocAsync(reinterpret_cast<void **>(&Jg), sizeof(TJ) * size_t(n) * pitch_of(n) * L.grid, st);
+        if (e != cudaSuccess) return set_error(PSR_E_OOM, "matrix slots for the block LU");
+    }
+    block_lu_kernel<TJ><<<L.grid, kBT, L.smem, st>>>(B, n, A, r, x, ok, Jg);
+    e = cudaGetLastError();
+    if (Jg) cudaFreeAsync(Jg, st);
+    if (e != cudaSuccess) return cuda_error("block_lu_kernel launch", e);
+    return PSR_OK;
+}
+
+int block_lu(int64_t B, int n, const double *A, const double *r, double *x, int32_t *ok, int precision,
+             cudaStream_t st) {
+    if (n > kMaxBlockN) return set_error(PSR_E_ARG, "psr_batch_lu_solve: n > 512");
+    return precision == PSR_MIXED ? block_lu_t<float>(B, n, A, r, x, ok, st) : block_lu_t<double>(B, n, A, r, x, ok, st);
+}
+
+}  // namespace psr

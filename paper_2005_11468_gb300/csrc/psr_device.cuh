@@ -1,0 +1,129 @@
+// Device-side pieces shared by the warp-per-reactor and block-per-reactor solvers:
+// per-call parameter blocks, warp reductions, NASA-7 thermo and the Troe falloff form.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "psr_internal.h"
+
+namespace psr {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+
+constexpr double kLn10 = 2.302585092994045684;
+
+// ---------------------------------------------------------------- warp helpers
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+__device__ __forceinline__ double wmax(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+__device__ __forceinline__ double wmin(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+
+// ---------------------------------------------------------------- per-call parameters
+struct Batch {
+    int64_t B;
+    const double *Y_in, *T_in, *tau, *P, *Y0, *T0, *rate_mult;
+    double *Y_out, *T_out, *fnorm;
+    int32_t *iters, *ts_steps, *status, *nfev;
+    const double *M_in, *M0;   // [B][6] soot moments (sooting mechanisms); M0 may be NULL
+    double *M_out;
+    const int32_t *list;       // optional work list of reactor indices (device), length *list_len
+    const int32_t *list_len;
+    int fallback;              // this launch re-solves the list in FP64 after a mixed launch
+};
+
+struct Opts {
+    double ftol, step_rtol, step_atol_y, step_atol_t, ts_rtol, ts_atol_y, dt0_over_tau, dt_shrink,
+        y_floor, t_min, t_max;
+    int max_newton, max_damp, max_ts_rounds, ts_steps, ts_newton, energy;
+};
+
+// Scalars of the last residual evaluation that the Jacobian reuses.
+struct Mix {
+    double T, lnT, invT, rho, Wbar, Ctot, lnPRT;
+    double N, cp, sum_yin_cp, sum_y_dcp;     // energy row pieces
+    double h_in;                             // sum_k Y_k,in h_k(T_in), per reactor
+};
+
+// ---------------------------------------------------------------- thermo (NASA-7)
+__device__ __forceinline__ void nasa7(const double *__restrict__ nasa, int k, double T, double lnT, double invT,
+                                      double &cpR, double &hRT, double &sR, double &dcpR) {
+    const double *c = nasa + size_t(k) * 16;
+    const double tmid = __ldg(c);
+    const double *a = c + (T < tmid ? 1 : 8);
+    const double a1 = __ldg(a), a2 = __ldg(a + 1), a3 = __ldg(a + 2), a4 = __ldg(a + 3), a5 = __ldg(a + 4),
+                 a6 = __ldg(a + 5), a7 = __ldg(a + 6);
+    constexpr double k3 = 1.0 / 3.0, k5 = 1.0 / 5.0;
+    cpR = a1 + T * (a2 + T * (a3 + T * (a4 + T * a5)));
+    hRT = a1 + T * (0.5 * a2 + T * (k3 * a3 + T * (0.25 * a4 + T * (k5 * a5)))) + a6 * invT;
+    sR = a1 * lnT + T * (a2 + T * (0.5 * a3 + T * (k3 * a4 + T * (0.25 * a5)))) + a7;
+    dcpR = a2 + T * (2 * a3 + T * (3 * a4 + T * 4 * a5));
+}
+
+// ---------------------------------------------------------------- Troe falloff pieces
+struct Troe {
+    double fac;       // P_r / (1 + P_r) F
+    double D;         // d ln(fac) / d ln P_r
+    double dlnF_dT;   // d ln F / dT at fixed P_r
+    double dlk0;      // d ln k0 / dT
+};
+
+__device__ __forceinline__ Troe troe_eval(const double *__restrict__ tp, double a_inf, double M, double T,
+                                          double lnT, double invT, bool want_deriv) {
+    Troe t;
+    const double lnA0 = __ldg(tp), b0 = __ldg(tp + 1), th0 = __ldg(tp + 2), al = __ldg(tp + 3),
+                 T3 = __ldg(tp + 4), T1 = __ldg(tp + 5), T2 = __ldg(tp + 6);
+    const double Pr = exp(lnA0 + b0 * lnT - th0 * invT - a_inf) * M;     // k0 [M] / k_inf
+    const double e3 = exp(-T / T3), e1 = exp(-T / T1);
+    const double e2 = (T2 != 0.0) ? exp(-T2 * invT) : 0.0;
+    const double Fc = (1.0 - al) * e3 + al * e1 + e2;
+    const double L = log10(Fc);
+    const double cc = -0.4 - 0.67 * L, nn = 0.75 - 1.27 * L;
+    const double u = log10(Pr) + cc;
+    const double den = nn - 0.14 * u;
+    const double f1 = u / den;
+    const double s = 1.0 + f1 * f1;
+    const double lgF = L / s;
+    const double F = exp(kLn10 * lgF);
+    t.fac = Pr / (1.0 + Pr) * F;
+    if (want_deriv) {
+        const double dlgF_du = -L * 2.0 * f1 / (s * s) * nn / (den * den);
+        t.D = 1.0 / (1.0 + Pr) + dlgF_du;
+        const double dFc = -(1.0 - al) / T3 * e3 - al / T1 * e1 + ((T2 != 0.0) ? T2 * invT * invT * e2 : 0.0);
+        const double dL_dT = dFc / (Fc * kLn10);
+        const double df1_dL = (-0.67 * nn + 1.27 * u) / (den * den);
+        const double dlgF_dL = 1.0 / s - L * 2.0 * f1 / (s * s) * df1_dL;
+        t.dlnF_dT = kLn10 * dlgF_dL * dL_dT;
+        t.dlk0 = b0 * invT + th0 * invT * invT;
+    } else {
+        t.D = t.dlnF_dT = t.dlk0 = 0.0;
+    }
+    return t;
+}
+
+// Host launchers of the block-per-reactor solver (psr_block.cu), for mechanisms whose
+// K + 1 unknowns exceed one warp's 64.
+int block_check(const Mech &m);
+int block_solve(const Mech &m, const Batch &bt, const Opts &o, int precision, bool fallback, int bps_req,
+                cudaStream_t st);
+int block_eval(const Mech &m, const Batch &bt, int energy, int want_J, int precision, double *out, cudaStream_t st);
+int block_adjoint(const Mech &m, const Batch &bt, int energy, const double *g, double *grad, double *lam_out,
+                  int32_t *ok, cudaStream_t st);
+int block_lu(int64_t B, int n, const double *A, const double *r, double *x, int32_t *ok, int precision,
+             cudaStream_t st);
+
+}  // namespace psr

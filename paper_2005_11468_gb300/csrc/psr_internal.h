@@ -39,7 +39,20 @@ struct DevMech {
     const int8_t *part_rm;       // [I][6] bit s: participant fills product slot s
     const int32_t *orig;         // [I] index of the reaction in the mechanism file
     int tb_first, troe_first;    // device order: elementary [0, tb_first), third-body, falloff [troe_first, I)
+    int nsoot;                   // 6 when the mechanism carries MOMIC soot constants, else 0
+    int soot_P, soot_H2;         // precursor and H2 species
+    const double *soot;          // kSoot* layout below
 };
+
+// Soot table layout (doubles).
+constexpr int kNMom = 6;
+constexpr int kSootNucLnA = 0, kSootNucTheta = 1, kSootCmin = 2, kSootGrowLnA = 3, kSootGrowBeta = 4,
+              kSootGrowTheta = 5, kSootGrowPref = 6, kSootKf = 7, kSootScale = 8 /* [6] s_r */,
+              kSootLnScale = 14 /* [6] ln s_r */, kSootW = 20 /* [29][6] fractional-moment weights */,
+              kSootWHalf = 20 + 29 * 6 /* [4] l = 1/2 weights */, kSootLen = 20 + 29 * 6 + 4;
+// fractional moments: index 3 j + c for p = j + 1/6 (c = 0), j - 1/6 (c = 1), j - 1/2 (c = 2),
+// j = 0..7 (coagulation); 24 + l for p = l + 2/3, l = 0..4 (growth)
+constexpr int kSootNFrac = 29;
 
 struct Mech {
     int K = 0, I = 0, E = 0, n_tb = 0, n_troe = 0, tb_first = 0, troe_first = 0;
@@ -62,6 +75,8 @@ struct Mech {
     std::vector<int32_t> orig;
     std::vector<double> soot;                  // raw soot constants (key order of the file)
     std::vector<std::string> soot_keys;
+    std::vector<double> soot_tab;              // kSootLen device table (empty without soot)
+    int soot_P = 0, soot_H2 = 0;
     int device = -1;
     void *dev_block = nullptr;                 // one device allocation for all tables
     DevMech dev{};

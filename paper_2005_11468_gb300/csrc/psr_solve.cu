@@ -17,37 +17,17 @@
 #include <cstring>
 #include <string>
 
+#include "psr_device.cuh"
 #include "psr_internal.h"
 
 namespace psr {
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
 
 // The per-reactor stages are inlined by default (measured ~7% faster on GB300 than
 // out-of-line copies); define PSR_STAGE=__noinline__ to keep one copy of each.
 #ifndef PSR_STAGE
 #define PSR_STAGE
 #endif
-constexpr double kLn10 = 2.302585092994045684;
-
-// ---------------------------------------------------------------- warp helpers
-__device__ __forceinline__ double wsum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
-__device__ __forceinline__ double wmax(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
-    return v;
-}
-__device__ __forceinline__ double wmin(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(kFull, v, o));
-    return v;
-}
-
 // A length-n vector distributed over the warp: lane l holds components l and l + 32.
 struct V2 {
     double a, b;
@@ -57,20 +37,6 @@ __device__ __forceinline__ double comp_get(const V2 &v, int j) {
     return x;
 }
 
-// ---------------------------------------------------------------- per-call parameters
-struct Batch {
-    int64_t B;
-    const double *Y_in, *T_in, *tau, *P, *Y0, *T0, *rate_mult;
-    double *Y_out, *T_out, *fnorm;
-    int32_t *iters, *ts_steps, *status, *nfev;
-};
-
-struct Opts {
-    double ftol, step_rtol, step_atol_y, step_atol_t, ts_rtol, ts_atol_y, dt0_over_tau, dt_shrink,
-        y_floor, t_min, t_max;
-    int max_newton, max_damp, max_ts_rounds, ts_steps, ts_newton, energy;
-};
-
 // Per-warp shared-memory workspace.
 template <class TJ>
 struct WS {
@@ -78,16 +44,19 @@ struct WS {
     double *kf, *kr, *q;     // [I]: effective rate constants of the last residual, q_i (or Euler sums)
     double *v;               // [K] dense third-body column part of the concentration Jacobian
     double *tD, *tX;         // [n_troe] falloff d ln(kf)/d ln Pr and the extra d ln(kf)/dT term
+    double *sfd;             // soot: [17][7] perturbed source evaluations, [7][8] derivatives
     TJ *J;                   // [n][P]
     TJ *rhs;                 // [n]
     int16_t *perm;           // [n] row order after pivoting
     int P;                   // row pitch of J (elements)
 };
 
+constexpr int kSootFD = 17 * 7 + 7 * 8;   // doubles of the soot finite-difference scratch
+
 template <class TJ>
-__host__ __device__ inline size_t ws_bytes(int K, int I, int n, int nt) {
+__host__ __device__ inline size_t ws_bytes(int K, int I, int n, int nt, int ns = 0) {
     int P = n + 1;
-    size_t b = sizeof(double) * (3 * (K + 1) + 3 * I + K + 2 * nt);
+    size_t b = sizeof(double) * (3 * (K + 1) + 3 * I + K + 2 * nt + (ns ? kSootFD : 0));
     b = (b + 15) & ~size_t(15);
     b += sizeof(TJ) * (size_t(n) * P + n);
     b = (b + 15) & ~size_t(15);
@@ -96,7 +65,7 @@ __host__ __device__ inline size_t ws_bytes(int K, int I, int n, int nt) {
 }
 
 template <class TJ>
-__device__ WS<TJ> carve(char *base, int K, int I, int n, int nt) {
+__device__ WS<TJ> carve(char *base, int K, int I, int n, int nt, int ns = 0) {
     WS<TJ> w;
     double *d = reinterpret_cast<double *>(base);
     w.C = d;
@@ -108,7 +77,8 @@ __device__ WS<TJ> carve(char *base, int K, int I, int n, int nt) {
     w.v = w.q + I;
     w.tD = w.v + K;
     w.tX = w.tD + nt;
-    size_t off = sizeof(double) * (3 * (K + 1) + 3 * I + K + 2 * nt);
+    w.sfd = w.tX + nt;
+    size_t off = sizeof(double) * (3 * (K + 1) + 3 * I + K + 2 * nt + (ns ? kSootFD : 0));
     off = (off + 15) & ~size_t(15);
     w.P = n + 1;
     w.J = reinterpret_cast<TJ *>(base + off);
@@ -119,72 +89,84 @@ __device__ WS<TJ> carve(char *base, int K, int I, int n, int nt) {
     return w;
 }
 
-// Scalars of the last residual evaluation that the Jacobian reuses.
-struct Mix {
-    double T, lnT, invT, rho, Wbar, Ctot, lnPRT;
-    double N, cp, sum_yin_cp, sum_y_dcp;     // energy row pieces
-    double h_in;                             // sum_k Y_k,in h_k(T_in), per reactor
-};
-
 // Lane-owned species data of the last residual evaluation.
 struct SpecLane {
     double cpR[2], dcpR[2];
 };
 
-// ---------------------------------------------------------------- thermo (NASA-7)
-__device__ __forceinline__ void nasa7(const double *__restrict__ nasa, int k, double T, double lnT, double invT,
-                                      double &cpR, double &hRT, double &sR, double &dcpR) {
-    const double *c = nasa + size_t(k) * 16;
-    const double tmid = __ldg(c);
-    const double *a = c + (T < tmid ? 1 : 8);
-    const double a1 = __ldg(a), a2 = __ldg(a + 1), a3 = __ldg(a + 2), a4 = __ldg(a + 3), a5 = __ldg(a + 4),
-                 a6 = __ldg(a + 5), a7 = __ldg(a + 6);
-    constexpr double k3 = 1.0 / 3.0, k5 = 1.0 / 5.0;
-    cpR = a1 + T * (a2 + T * (a3 + T * (a4 + T * a5)));
-    hRT = a1 + T * (0.5 * a2 + T * (k3 * a3 + T * (0.25 * a4 + T * (k5 * a5)))) + a6 * invT;
-    sR = a1 * lnT + T * (a2 + T * (0.5 * a3 + T * (k3 * a4 + T * (0.25 * a5)))) + a7;
-    dcpR = a2 + T * (2 * a3 + T * (3 * a4 + T * 4 * a5));
-}
-
-// ---------------------------------------------------------------- Troe falloff pieces
-struct Troe {
-    double fac;       // P_r / (1 + P_r) F
-    double D;         // d ln(fac) / d ln P_r
-    double dlnF_dT;   // d ln F / dT at fixed P_r
-    double dlk0;      // d ln k0 / dT
-};
-
-__device__ __forceinline__ Troe troe_eval(const double *__restrict__ tp, double a_inf, double M, double T,
-                                          double lnT, double invT, bool want_deriv) {
-    Troe t;
-    const double lnA0 = __ldg(tp), b0 = __ldg(tp + 1), th0 = __ldg(tp + 2), al = __ldg(tp + 3),
-                 T3 = __ldg(tp + 4), T1 = __ldg(tp + 5), T2 = __ldg(tp + 6);
-    const double Pr = exp(lnA0 + b0 * lnT - th0 * invT - a_inf) * M;     // k0 [M] / k_inf
-    const double e3 = exp(-T / T3), e1 = exp(-T / T1);
-    const double e2 = (T2 != 0.0) ? exp(-T2 * invT) : 0.0;
-    const double Fc = (1.0 - al) * e3 + al * e1 + e2;
-    const double L = log10(Fc);
-    const double cc = -0.4 - 0.67 * L, nn = 0.75 - 1.27 * L;
-    const double u = log10(Pr) + cc;
-    const double den = nn - 0.14 * u;
-    const double f1 = u / den;
-    const double s = 1.0 + f1 * f1;
-    const double lgF = L / s;
-    const double F = exp(kLn10 * lgF);
-    t.fac = Pr / (1.0 + Pr) * F;
-    if (want_deriv) {
-        const double dlgF_du = -L * 2.0 * f1 / (s * s) * nn / (den * den);
-        t.D = 1.0 / (1.0 + Pr) + dlgF_du;
-        const double dFc = -(1.0 - al) / T3 * e3 - al / T1 * e1 + ((T2 != 0.0) ? T2 * invT * invT * e2 : 0.0);
-        const double dL_dT = dFc / (Fc * kLn10);
-        const double df1_dL = (-0.67 * nn + 1.27 * u) / (den * den);
-        const double dlgF_dL = 1.0 / s - L * 2.0 * f1 / (s * s) * df1_dL;
-        t.dlnF_dT = kLn10 * dlgF_dL * dL_dT;
-        t.dlk0 = b0 * invT + th0 * invT * invT;
-    } else {
-        t.D = t.dlnF_dT = t.dlk0 = 0.0;
+// ---------------------------------------------------------------- MOMIC soot sources
+// Moment sources S_r = R_r + W_r + G_r (r = 0..5) and the precursor sink (mol/cm^3/s) at
+// log moments z_r = ln(M_r / s_r), precursor concentration CP and temperature T:
+// nucleation R_r = J C_min^r, J = A_n exp(-theta_n/T) CP N_A; growth
+// W_r = k_g CP chi_alpha pi d_C^2 M_0 sum_{l<r} C(r,l) mu_{l+2/3} 2^(r-l); free-molecular
+// coagulation G_0 = -K_f M_0^2 f_{0,0}/2, G_1 = 0, G_r = K_f M_0^2/2 sum_k C(r,k) f_{k,r-k}
+// with f = f(1/2) interpolated in log over the grid functions f(l), l = 0..3; fractional
+// moments mu_p = exp(sum_r w_r(p) ln mu_r) with the loader's Lagrange weights.
+__device__ __forceinline__ void soot_eval(const double *__restrict__ st, const double *z, double CP, double T,
+                                          double *S, double &sink) {
+    constexpr double kNA = 6.02214076e23;
+    const double lnT = log(T), invT = 1.0 / T;
+    const double lnM0 = __ldg(st + kSootLnScale) + z[0];
+    const double M0 = exp(lnM0);
+    double lnmu[kNMom];
+#pragma unroll
+    for (int r = 0; r < kNMom; ++r) lnmu[r] = __ldg(st + kSootLnScale + r) + z[r] - lnM0;
+    double mu[kSootNFrac];
+#pragma unroll
+    for (int i = 0; i < kSootNFrac; ++i) {
+        double acc = 0.0;
+#pragma unroll
+        for (int r = 1; r < kNMom; ++r) acc += __ldg(st + kSootW + i * kNMom + r) * lnmu[r];
+        mu[i] = exp(acc);
     }
-    return t;
+    const double cmin = __ldg(st + kSootCmin);
+    const double J = exp(__ldg(st + kSootNucLnA) - __ldg(st + kSootNucTheta) * invT) * CP * kNA;
+    const double kg = exp(__ldg(st + kSootGrowLnA) + __ldg(st + kSootGrowBeta) * lnT - __ldg(st + kSootGrowTheta) * invT);
+    const double pref = kg * CP * __ldg(st + kSootGrowPref) * M0;
+    // growth: W_r = pref sum_{l<r} C(r, l) mu_{l+2/3} 2^(r-l)
+    const double g0 = mu[24], g1 = mu[25], g2 = mu[26], g3 = mu[27], g4 = mu[28];
+    double W[kNMom];
+    W[0] = 0.0;
+    W[1] = pref * (2.0 * g0);
+    W[2] = pref * (4.0 * g0 + 2.0 * 2.0 * g1);
+    W[3] = pref * (8.0 * g0 + 3.0 * 4.0 * g1 + 3.0 * 2.0 * g2);
+    W[4] = pref * (16.0 * g0 + 4.0 * 8.0 * g1 + 6.0 * 4.0 * g2 + 4.0 * 2.0 * g3);
+    W[5] = pref * (32.0 * g0 + 5.0 * 16.0 * g1 + 10.0 * 8.0 * g2 + 10.0 * 4.0 * g3 + 5.0 * 2.0 * g4);
+    // coagulation: f(1/2) for the pairs (0,0) (1,1) (1,2) (1,3) (2,2) (1,4) (2,3)
+    const double beta = __ldg(st + kSootKf) * sqrt(T) * M0 * M0;
+    const int px[7] = {0, 1, 1, 1, 2, 1, 2}, py[7] = {0, 1, 2, 3, 2, 4, 3};
+    const double binom[4][4] = {{1, 0, 0, 0}, {1, 1, 0, 0}, {1, 2, 1, 0}, {1, 3, 3, 1}};
+    double fh[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        const int x = px[q], y = py[q];
+        double lf = 0.0;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            double f = 0.0;
+#pragma unroll
+            for (int k = 0; k <= l; ++k) {
+                const int a = k + x, b = l - k + y;
+                f += binom[l][k] * (mu[3 * a] * mu[3 * b + 2] + 2.0 * mu[3 * a + 1] * mu[3 * b + 1] + mu[3 * a + 2] * mu[3 * b]);
+            }
+            lf += __ldg(st + kSootWHalf + l) * log(f);
+        }
+        fh[q] = exp(lf);
+    }
+    double G[kNMom];
+    G[0] = -0.5 * beta * fh[0];
+    G[1] = 0.0;
+    G[2] = 0.5 * beta * (2.0 * fh[1]);
+    G[3] = 0.5 * beta * (6.0 * fh[2]);
+    G[4] = 0.5 * beta * (8.0 * fh[3] + 6.0 * fh[4]);
+    G[5] = 0.5 * beta * (10.0 * fh[5] + 20.0 * fh[6]);
+    double cr = 1.0;
+#pragma unroll
+    for (int r = 0; r < kNMom; ++r) {
+        S[r] = J * cr + W[r] + G[r];
+        cr *= cmin;
+    }
+    sink = (J * cmin + W[1]) / (2.0 * kNA);
 }
 
 // ---------------------------------------------------------------- residual, Eqs. (2)-(9)
@@ -192,7 +174,7 @@ __device__ __forceinline__ Troe troe_eval(const double *__restrict__ tp, double 
 // memory and the scalars/lane data in mx/sl for the Jacobian.
 template <class TJ>
 __device__ PSR_STAGE void eval_F(const DevMech &M, const WS<TJ> &w, const V2 &y, V2 &F, Mix &mx, SpecLane &sl,
-                       const double *Yin_row, double tau, double P, double Tspec, int energy,
+                       const double *Yin_row, const double *Min, double tau, double P, double Tspec, int energy,
                        const double *__restrict__ mult) {
     const int lane = threadIdx.x & 31;
     const int K = M.K, I = M.I;
@@ -305,7 +287,15 @@ __device__ PSR_STAGE void eval_F(const DevMech &M, const WS<TJ> &w, const V2 &y,
         w.q[i] = q;
     }
     __syncwarp();
-    // Eq. (4) and the species residuals of Eq. (2); wdot_k is left in v[] for the Jacobian
+    // MOMIC sources (every lane evaluates them; the warp pays for one evaluation)
+    double Ssoot[kNMom], sink = 0.0, zs[kNMom];
+    if (M.nsoot) {
+#pragma unroll
+        for (int r = 0; r < kNMom; ++r) zs[r] = comp_get(y, K + 1 + r);
+        soot_eval(M.soot, zs, w.C[M.soot_P], T, Ssoot, sink);
+    }
+    // Eq. (4) (plus the soot sink on precursor and H2) and the species residuals of
+    // Eq. (2); wdot_k is left in v[] for the Jacobian
     double s_hw = 0.0;
     const double tau_rho = tau / rho;
     F.a = 0.0;
@@ -321,7 +311,8 @@ __device__ PSR_STAGE void eval_F(const DevMech &M, const WS<TJ> &w, const V2 &y,
                 w1 += __ldg(M.sp_nu_d + e + 1) * w.q[__ldg(M.sp_rxn + e + 1)];
             }
             if (e < e_end) w0 += __ldg(M.sp_nu_d + e) * w.q[__ldg(M.sp_rxn + e)];
-            const double wd = w0 + w1;
+            double wd = w0 + w1;
+            if (M.nsoot) wd += (j == M.soot_H2 ? sink : 0.0) - (j == M.soot_P ? sink : 0.0);
             const double Yj = h ? y.b : y.a;
             const double f = Yj - Yin_row[j] - tau_rho * __ldg(M.W + j) * wd;
             s_hw += w.hRT[j] * wd;
@@ -347,6 +338,23 @@ __device__ PSR_STAGE void eval_F(const DevMech &M, const WS<TJ> &w, const V2 &y,
         if (K < 32) F.a = FT;
         else F.b = FT;
     }
+    // moment balances F_r = (M_r - M_r,in - tau S_r) / (M_r + s_r)
+    if (M.nsoot) {
+        for (int h = 0; h < 2; ++h) {
+            const int j = lane + 32 * h;
+            if (j > K && j <= K + kNMom) {
+                const int r = j - K - 1;
+                const double sr = __ldg(M.soot + kSootScale + r);
+                const double Mr = sr * exp(h ? y.b : y.a);
+                double Sr = 0.0;
+#pragma unroll
+                for (int q = 0; q < kNMom; ++q) Sr = (q == r) ? Ssoot[q] : Sr;
+                const double f = (Mr - Min[r] - tau * Sr) / (Mr + sr);
+                if (h) F.b = f;
+                else F.a = f;
+            }
+        }
+    }
     __syncwarp();
 }
 
@@ -359,10 +367,10 @@ __device__ PSR_STAGE void eval_F(const DevMech &M, const WS<TJ> &w, const V2 &y,
 // rho(Y, T) and the energy row of Eq. (3). Entries are accumulated in TJ.
 template <class TJ>
 __device__ PSR_STAGE void eval_J(const DevMech &M, const WS<TJ> &w, const V2 &y, const V2 &c, const Mix &mx,
-                                 const SpecLane &sl, const double *Yin_row, double tau, int energy,
-                                 const double *__restrict__ mult) {
+                                 const SpecLane &sl, const double *Yin_row, const double *Min, double tau,
+                                 int energy, const double *__restrict__ mult) {
     const int lane = threadIdx.x & 31;
-    const int K = M.K, I = M.I, n = K + 1, P = w.P;
+    const int K = M.K, I = M.I, n = K + 1 + M.nsoot, P = w.P;
     // wdot (left in v[] by eval_F) moves to registers; v[] becomes the dense part
     double wd[2];
     for (int h = 0; h < 2; ++h) {
@@ -538,6 +546,85 @@ __device__ PSR_STAGE void eval_J(const DevMech &M, const WS<TJ> &w, const V2 &y,
         }
     }
     __syncwarp();
+    if (M.nsoot) {
+        // soot couplings: central differences of the source function in (zeta_0..5, CP, T),
+        // lanes 0..16 each evaluating one perturbed input, chained through CP(Y, T)
+        const int Psp = M.soot_P, Hsp = M.soot_H2;
+        const double CP = w.C[Psp];
+        double z[kNMom];
+#pragma unroll
+        for (int r = 0; r < kNMom; ++r) z[r] = comp_get(y, K + 1 + r);
+        const double hz = 1e-5, hC = 1e-3 * CP + 1e-9 * mx.Ctot, hT = 1e-5 * T;
+        {
+            double zi[kNMom];
+#pragma unroll
+            for (int r = 0; r < kNMom; ++r) zi[r] = z[r];
+            double CPi = CP, Ti = T;
+            const int t = lane < 17 ? lane : 0;
+            const int inp = (t >= 1 && t <= 8) ? t - 1 : ((t >= 9) ? t - 9 : -1);
+            const double sg = (t >= 9) ? -1.0 : 1.0;
+#pragma unroll
+            for (int r = 0; r < kNMom; ++r) zi[r] += (inp == r) ? sg * hz : 0.0;
+            if (inp == 6) CPi += sg * hC;
+            if (inp == 7) Ti += sg * hT;
+            double Sx[kNMom], sx;
+            soot_eval(M.soot, zi, CPi, Ti, Sx, sx);
+            if (lane < 17) {
+#pragma unroll
+                for (int r = 0; r < kNMom; ++r) w.sfd[lane * 7 + r] = Sx[r];
+                w.sfd[lane * 7 + 6] = sx;
+            }
+        }
+        __syncwarp();
+        double *D = w.sfd + 17 * 7;          // D[o][i]: o = S_0..S_5, sink; i = zeta_0..5, CP, T
+        for (int idx = lane; idx < 56; idx += 32) {
+            const int o = idx / 8, i = idx % 8;
+            const double h = (i < 6) ? hz : (i == 6 ? hC : hT);
+            D[idx] = (w.sfd[(1 + i) * 7 + o] - w.sfd[(9 + i) * 7 + o]) / (2.0 * h);
+        }
+        __syncwarp();
+        const double invWP = __ldg(M.invW + Psp);
+        const double RT = kRu * T;
+        const double eco = (energy == PSR_FIXED_T) ? 0.0
+                               : (tau / mx.rho) * (w.hRT[Hsp] - w.hRT[Psp]) * RT / (mx.cp * T);
+        // rows: 0 precursor, 1 H2, 2 energy, 3..8 moments
+        for (int idx = lane; idx < 9 * n; idx += 32) {
+            const int rk = idx / n, j = idx % n;
+            // d(input)/dx_j for the source inputs
+            auto dsrc = [&](int o) {
+                const double dCP = (j < K) ? ((j == Psp ? mx.rho * invWP : 0.0) - CP * mx.Wbar * __ldg(M.invW + j))
+                                           : (j == K ? -CP * invT : 0.0);
+                double v = D[o * 8 + 6] * dCP;
+                if (j == K) v += D[o * 8 + 7];
+                if (j > K) v += D[o * 8 + (j - K - 1)];
+                return v;
+            };
+            double val;
+            int row;
+            if (rk == 0) {
+                row = Psp;
+                val = tau * __ldg(M.W + Psp) / mx.rho * dsrc(6);
+            } else if (rk == 1) {
+                row = Hsp;
+                val = -tau * __ldg(M.W + Hsp) / mx.rho * dsrc(6);
+            } else if (rk == 2) {
+                row = K;
+                val = eco * dsrc(6);
+            } else {
+                const int r = rk - 3;
+                row = K + 1 + r;
+                const double sr = __ldg(M.soot + kSootScale + r);
+                const double Mr = sr * exp(z[r]);
+                const double den = Mr + sr;
+                const double num = Mr - Min[r] - tau * w.sfd[r];
+                val = -tau * dsrc(r) / den;
+                if (j == K + 1 + r) val += Mr / den - num * Mr / (den * den);
+            }
+            TJ *e = w.J + size_t(row) * P + j;
+            *e = TJ(double(*e) + val);
+        }
+        __syncwarp();
+    }
     // + diag(c)
     for (int h = 0; h < 2; ++h) {
         int j = lane + 32 * h;
@@ -695,6 +782,7 @@ __device__ void lu_solve_T(const WS<TJ> &w, int n, const V2 &g, V2 &lam) {
 // ---------------------------------------------------------------- solver pieces
 struct Reactor {
     const double *Yin;
+    const double *Min;   // [6] inlet soot moments (sooting mechanisms)
     double tau, P, Tspec;
 };
 
@@ -702,13 +790,13 @@ __device__ __forceinline__ bool all_finite(const V2 &v) {
     return __all_sync(kFull, isfinite(v.a) && isfinite(v.b));
 }
 
-// mass fractions absolute, temperature relative
-__device__ __forceinline__ double scaled_max(const V2 &dy, const V2 &y, int K) {
+// mass fractions and log moments absolute, temperature relative
+__device__ __forceinline__ double scaled_max(const V2 &dy, const V2 &y, int K, int n) {
     const int lane = threadIdx.x & 31;
     double m = 0.0;
     for (int h = 0; h < 2; ++h) {
         int j = lane + 32 * h;
-        if (j <= K) {
+        if (j < n) {
             double d = fabs(h ? dy.b : dy.a);
             if (j == K) d /= fabs(h ? y.b : y.a);
             m = fmax(m, d);
@@ -743,15 +831,17 @@ __device__ __forceinline__ double max_in_bounds(const V2 &y, const V2 &dy, int K
     return wmin(lam);
 }
 
-__device__ __forceinline__ bool step_small(const V2 &dy, const V2 &y, int K, double rtol, double atol_y,
-                                           double atol_t) {
+// |dx_j| <= rtol |x_j| + atol_j (species, temperature); |d zeta_r| <= atol_z (log moments)
+__device__ __forceinline__ bool step_small(const V2 &dy, const V2 &y, int K, int n, double rtol, double atol_y,
+                                           double atol_t, double atol_z) {
     const int lane = threadIdx.x & 31;
     bool ok = true;
     for (int h = 0; h < 2; ++h) {
         int j = lane + 32 * h;
-        if (j <= K) {
+        if (j < n) {
             const double x = h ? y.b : y.a, d = h ? dy.b : dy.a;
-            ok = ok && (fabs(d) <= rtol * fabs(x) + ((j < K) ? atol_y : atol_t));
+            if (j <= K) ok = ok && (fabs(d) <= rtol * fabs(x) + ((j < K) ? atol_y : atol_t));
+            else ok = ok && (fabs(d) <= atol_z);
         }
     }
     return __all_sync(kFull, ok);
@@ -773,7 +863,7 @@ struct Ctx {
 template <class TJ>
 __device__ void residual_R(Ctx &cx, const WS<TJ> &w, const V2 &y, const V2 &c, const V2 &xref, V2 &F, V2 &R) {
     ++cx.nfev;
-    eval_F(cx.M, w, y, F, cx.mx, cx.sl, cx.r.Yin, cx.r.tau, cx.r.P, cx.r.Tspec, cx.o.energy, cx.mult);
+    eval_F(cx.M, w, y, F, cx.mx, cx.sl, cx.r.Yin, cx.r.Min, cx.r.tau, cx.r.P, cx.r.Tspec, cx.o.energy, cx.mult);
     R.a = F.a + c.a * (y.a - xref.a);
     R.b = F.b + c.b * (y.b - xref.b);
 }
@@ -790,22 +880,22 @@ __device__ bool damped_newton(Ctx &cx, const WS<TJ> &w, V2 &y, const V2 &xref, c
     for (int it = 0; it < max_it; ++it) {
         if (counter >= o.max_newton) break;
         ++counter;
-        eval_J(cx.M, w, y, c, cx.mx, cx.sl, cx.r.Yin, cx.r.tau, o.energy, cx.mult);
+        eval_J(cx.M, w, y, c, cx.mx, cx.sl, cx.r.Yin, cx.r.Min, cx.r.tau, o.energy, cx.mult);
         if (!lu_factor(w, n)) break;
         V2 dy;
         lu_solve_neg(w, n, R, dy);
         if (!all_finite(dy)) break;
         if (steady) {
             const double rmax = wmax(fmax(fabs(R.a), fabs(R.b)));
-            if (rmax <= o.ftol && step_small(dy, y, K, o.step_rtol, o.step_atol_y, o.step_atol_t)) {
+            if (rmax <= o.ftol && step_small(dy, y, K, n, o.step_rtol, o.step_atol_y, o.step_atol_t, o.step_rtol)) {
                 y = axpy(y, 1.0, dy);
                 return true;
             }
-        } else if (step_small(dy, y, K, o.ts_rtol, o.ts_atol_y, o.ts_rtol)) {
+        } else if (step_small(dy, y, K, n, o.ts_rtol, o.ts_atol_y, o.ts_rtol, o.ts_rtol)) {
             y = axpy(y, 1.0, dy);
             return true;
         }
-        const double dn = scaled_max(dy, y, K);
+        const double dn = scaled_max(dy, y, K, n);
         if (dn >= dn_prev) break;
         dn_prev = dn;
         double lam = fmin(1.0, max_in_bounds(y, dy, K, o));
@@ -819,7 +909,7 @@ __device__ bool damped_newton(Ctx &cx, const WS<TJ> &w, V2 &y, const V2 &xref, c
                 if (all_finite(Rt)) {
                     V2 db;
                     lu_solve_neg(w, n, Rt, db);
-                    if (scaled_max(db, y, K) < dn) {
+                    if (scaled_max(db, y, K, n) < dn) {
                         accepted = true;
                         break;
                     }
@@ -834,6 +924,48 @@ __device__ bool damped_newton(Ctx &cx, const WS<TJ> &w, V2 &y, const V2 &xref, c
     return false;
 }
 
+// Initial log moments: the given M0, or the nucleation-only steady state at the initial
+// gas state, M_r = M_r,in + tau J C_min^r.
+__device__ void init_moments(Ctx &cx, const Batch &bt, int64_t r, V2 &x) {
+    const int lane = threadIdx.x & 31;
+    const int K = cx.K;
+    const double *st = cx.M.soot;
+    double Mr[kNMom];
+    if (bt.M0) {
+#pragma unroll
+        for (int q = 0; q < kNMom; ++q) Mr[q] = bt.M0[r * kNMom + q];
+    } else {
+        double sYW = 0.0;
+        for (int h = 0; h < 2; ++h) {
+            const int j = lane + 32 * h;
+            if (j < K) sYW += (h ? x.b : x.a) * __ldg(cx.M.invW + j);
+        }
+        sYW = wsum(sYW);
+        const double T0 = comp_get(x, K);
+        const double YP = comp_get(x, cx.M.soot_P);
+        const double rho = cx.r.P / (sYW * kRu * T0);
+        const double CP = rho * YP * __ldg(cx.M.invW + cx.M.soot_P);
+        const double J = exp(__ldg(st + kSootNucLnA) - __ldg(st + kSootNucTheta) / T0) * CP * 6.02214076e23;
+        double cr = 1.0;
+#pragma unroll
+        for (int q = 0; q < kNMom; ++q) {
+            Mr[q] = cx.r.Min[q] + cx.r.tau * J * cr;
+            cr *= __ldg(st + kSootCmin);
+        }
+    }
+    for (int h = 0; h < 2; ++h) {
+        const int j = lane + 32 * h;
+        if (j > K && j <= K + kNMom) {
+            double m = 0.0;
+#pragma unroll
+            for (int q = 0; q < kNMom; ++q) m = (q == j - K - 1) ? Mr[q] : m;
+            const double z = log(m / __ldg(st + kSootScale + (j - K - 1)));
+            if (h) x.b = z;
+            else x.a = z;
+        }
+    }
+}
+
 template <class TJ>
 __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) {
     const int lane = threadIdx.x & 31;
@@ -841,6 +973,7 @@ __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) 
     const Opts &o = cx.o;
     const double tau = bt.tau[r];
     cx.r.Yin = bt.Y_in + r * K;
+    cx.r.Min = (cx.M.nsoot && bt.M_in) ? bt.M_in + r * kNMom : nullptr;
     cx.r.tau = tau;
     cx.r.P = bt.P[r];
     cx.r.Tspec = bt.T0[r];
@@ -862,6 +995,7 @@ __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) 
     V2 x;
     x.a = (lane < K) ? bt.Y0[r * K + lane] : (lane == K ? bt.T0[r] : 0.0);
     x.b = (lane + 32 < K) ? bt.Y0[r * K + lane + 32] : (lane + 32 == K ? bt.T0[r] : 0.0);
+    if (cx.M.nsoot) init_moments(cx, bt, r, x);
     const V2 zero{0.0, 0.0};
     V2 F, R;
     residual_R(cx, w, x, zero, x, F, R);
@@ -896,8 +1030,9 @@ __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) 
                 const double Tx = comp_get(x, K);
                 const double s = tau / dt;
                 V2 c;
-                c.a = (lane < K) ? s : (lane == K ? (o.energy == PSR_FIXED_T ? s : s / Tx) : 0.0);
-                c.b = (lane + 32 < K) ? s : (lane + 32 == K ? (o.energy == PSR_FIXED_T ? s : s / Tx) : 0.0);
+                const double sT = (o.energy == PSR_FIXED_T) ? s : s / Tx;
+                c.a = (lane < K) ? s : (lane == K ? sT : (lane < cx.n ? s : 0.0));
+                c.b = (lane + 32 < K) ? s : (lane + 32 == K ? sT : (lane + 32 < cx.n ? s : 0.0));
                 const int used0 = counter;
                 V2 y = x;
                 bool ok = damped_newton(cx, w, y, x, c, o.ts_newton, false, counter);
@@ -933,13 +1068,21 @@ __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) 
     if (lane < K) bt.Y_out[r * K + lane] = out.a;
     if (lane + 32 < K) bt.Y_out[r * K + lane + 32] = out.b;
     const double Tout = comp_get(out, K);
+    if (cx.M.nsoot && bt.M_out) {
+        for (int h = 0; h < 2; ++h) {
+            const int j = lane + 32 * h;
+            if (j > K && j <= K + kNMom)
+                bt.M_out[r * kNMom + (j - K - 1)] = __ldg(cx.M.soot + kSootScale + (j - K - 1)) * exp(h ? out.b : out.a);
+        }
+    }
     if (lane == 0) {
         bt.T_out[r] = Tout;
-        if (bt.status) bt.status[r] = status;
-        if (bt.iters) bt.iters[r] = counter;
-        if (bt.ts_steps) bt.ts_steps[r] = ts;
+        const bool fb = bt.fallback != 0;
+        if (bt.status) bt.status[r] = (fb && status == PSR_CONVERGED) ? PSR_REFINE_FALLBACK : status;
+        if (bt.iters) bt.iters[r] = counter + (fb ? bt.iters[r] : 0);
+        if (bt.ts_steps) bt.ts_steps[r] = ts + (fb ? bt.ts_steps[r] : 0);
         if (bt.fnorm) bt.fnorm[r] = fn;
-        if (bt.nfev) bt.nfev[r] = cx.nfev;
+        if (bt.nfev) bt.nfev[r] = cx.nfev + (fb ? bt.nfev[r] : 0);
     }
 }
 
@@ -955,20 +1098,28 @@ __global__ void __launch_bounds__(128, PSR_MIN_BLOCKS) solve_kernel(DevMech M, B
                                                                    size_t ws_per_warp) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WS<TJ> w = carve<TJ>(smem + warp * ws_per_warp, M.K, M.I, M.K + 1, M.n_troe);
+    WS<TJ> w = carve<TJ>(smem + warp * ws_per_warp, M.K, M.I, M.K + 1 + M.nsoot, M.n_troe, M.nsoot);
     Ctx cx;
     cx.M = M;
     cx.o = o;
     cx.mult = bt.rate_mult;
     cx.K = M.K;
-    cx.n = M.K + 1;
+    cx.n = M.K + 1 + M.nsoot;
+    const int64_t nwork = bt.list ? int64_t(*bt.list_len) : bt.B;
     while (true) {
-        int r = 0;
-        if (lane == 0) r = atomicAdd(queue, 1);
-        r = __shfl_sync(kFull, r, 0);
-        if (r >= bt.B) break;
+        int p = 0;
+        if (lane == 0) p = atomicAdd(queue, 1);
+        p = __shfl_sync(kFull, p, 0);
+        if (p >= nwork) break;
+        const int64_t r = bt.list ? int64_t(bt.list[p]) : int64_t(p);
         solve_one<TJ>(cx, w, bt, r);
     }
+}
+
+// Work list of the reactors a mixed-precision launch left unconverged.
+__global__ void collect_unconverged(int64_t B, const int32_t *status, int32_t *list, int32_t *len) {
+    const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (r < B && status[r] != PSR_CONVERGED) list[atomicAdd(len, 1)] = int32_t(r);
 }
 
 // residual / Jacobian at given states: one warp per state
@@ -978,15 +1129,16 @@ __global__ void eval_kernel(DevMech M, Batch bt, int energy, int want_J, double 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r = int64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
     if (r >= bt.B) return;
-    WS<TJ> w = carve<TJ>(smem + warp * ws_per_warp, M.K, M.I, M.K + 1, M.n_troe);
+    WS<TJ> w = carve<TJ>(smem + warp * ws_per_warp, M.K, M.I, M.K + 1 + M.nsoot, M.n_troe, M.nsoot);
     Ctx cx;
     cx.M = M;
     cx.mult = bt.rate_mult;
     cx.K = M.K;
-    cx.n = M.K + 1;
+    cx.n = M.K + 1 + M.nsoot;
     cx.o.energy = energy;
-    const int K = M.K, n = K + 1;
+    const int K = M.K, n = cx.n;
     cx.r.Yin = bt.Y_in + r * K;
+    cx.r.Min = M.nsoot ? bt.M_in + r * kNMom : nullptr;
     cx.r.tau = bt.tau[r];
     cx.r.P = bt.P[r];
     cx.r.Tspec = bt.T0[r];
@@ -1006,6 +1158,7 @@ __global__ void eval_kernel(DevMech M, Batch bt, int energy, int want_J, double 
     V2 y;
     y.a = (lane < K) ? bt.Y0[r * K + lane] : (lane == K ? bt.T0[r] : 0.0);
     y.b = (lane + 32 < K) ? bt.Y0[r * K + lane + 32] : (lane + 32 == K ? bt.T0[r] : 0.0);
+    if (M.nsoot) init_moments(cx, bt, r, y);       // bt.M0 holds the state's moments
     const V2 zero{0.0, 0.0};
     V2 F, R;
     residual_R(cx, w, y, zero, y, F, R);
@@ -1014,7 +1167,7 @@ __global__ void eval_kernel(DevMech M, Batch bt, int energy, int want_J, double 
         if (lane + 32 < n) out[r * n + lane + 32] = F.b;
         return;
     }
-    eval_J(M, w, y, zero, cx.mx, cx.sl, cx.r.Yin, cx.r.tau, energy, cx.mult);
+    eval_J(M, w, y, zero, cx.mx, cx.sl, cx.r.Yin, cx.r.Min, cx.r.tau, energy, cx.mult);
     for (int idx = lane; idx < n * n; idx += 32)
         out[r * n * n + idx] = double(w.J[size_t(idx / n) * w.P + idx % n]);
 }
@@ -1059,7 +1212,8 @@ __global__ void adjoint_kernel(DevMech M, Batch bt, int energy, const double *g,
     const V2 zero{0.0, 0.0};
     V2 F, R;
     residual_R(cx, w, y, zero, y, F, R);
-    eval_J(M, w, y, zero, cx.mx, cx.sl, cx.r.Yin, cx.r.tau, energy, cx.mult);
+    cx.r.Min = nullptr;
+    eval_J(M, w, y, zero, cx.mx, cx.sl, cx.r.Yin, nullptr, cx.r.tau, energy, cx.mult);
     const bool good = lu_factor(w, n);
     V2 gv, lam{0.0, 0.0};
     gv.a = (lane < n) ? g[r * n + lane] : 0.0;
@@ -1156,14 +1310,15 @@ int check_opts(const psr_options *po) {
         s.max_ts_rounds < 0 || s.ts_steps < 1 || s.ts_newton < 1 ||
         (s.precision != PSR_FP64 && s.precision != PSR_MIXED) ||
         (s.energy != PSR_ADIABATIC && s.energy != PSR_FIXED_T) || s.warps_per_block < 0 || s.warps_per_block > 32 ||
-        s.blocks_per_sm < 0)
+        s.blocks_per_sm < 0 || (s.mixed_fallback != 0 && s.mixed_fallback != 1))
         return set_error(PSR_E_ARG, "psr_options: value out of range");
     return PSR_OK;
 }
 
 template <class TJ>
-int launch_solve(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int bps_req, cudaStream_t st) {
-    const size_t wsb = ws_bytes<TJ>(m.K, m.I, m.K + 1, m.n_troe);
+int launch_solve_q(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int bps_req, cudaStream_t st,
+                   int *queue) {
+    const size_t wsb = ws_bytes<TJ>(m.K, m.I, m.K + 1 + m.dev.nsoot, m.n_troe, m.dev.nsoot);
     int dev = 0;
     cudaGetDevice(&dev);
     int max_smem = 0, nsm = 0;
@@ -1184,21 +1339,60 @@ int launch_solve(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int
     int64_t want = (bt.B + wpb - 1) / wpb;
     int64_t grid = std::min<int64_t>(int64_t(per_sm) * nsm, want);
     if (grid < 1) grid = 1;
-    int *queue = nullptr;
-    e = cudaMallocAsync(reinterpret_cast<void **>(&queue), sizeof(int), st);
-    if (e != cudaSuccess) return set_error(PSR_E_OOM, "work-queue allocation failed");
-    cudaMemsetAsync(queue, 0, sizeof(int), st);
-    DevMech D = m.dev;
-    solve_kernel<TJ><<<unsigned(grid), wpb * 32, smem, st>>>(D, bt, o, queue, wsb);
+    e = cudaMemsetAsync(queue, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_error("cudaMemsetAsync(work queue)", e);
+    solve_kernel<TJ><<<unsigned(grid), wpb * 32, smem, st>>>(m.dev, bt, o, queue, wsb);
     e = cudaGetLastError();
-    cudaFreeAsync(queue, st);
     if (e != cudaSuccess) return cuda_error("solve_kernel launch", e);
     return PSR_OK;
 }
 
 template <class TJ>
+int launch_solve(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int bps_req, cudaStream_t st) {
+    int *queue = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&queue), sizeof(int), st);
+    if (e != cudaSuccess) return set_error(PSR_E_OOM, "work-queue allocation failed");
+    const int rc = launch_solve_q<TJ>(m, bt, o, wpb_req, bps_req, st, queue);
+    cudaFreeAsync(queue, st);
+    return rc;
+}
+
+// Mixed form with per-reactor FP64 fallback: the FP32-Jacobian launch, then the reactors
+// it left unconverged (a device-side list, no host synchronisation) solved again from
+// their initial guesses with the FP64 Jacobian; those that converge get
+// PSR_REFINE_FALLBACK and their iteration counts add up.
+int launch_mixed(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int bps_req, bool fallback,
+                 cudaStream_t st) {
+    if (!fallback) return launch_solve<float>(m, bt, o, wpb_req, bps_req, st);
+    const size_t B = size_t(bt.B);
+    int32_t *scr = nullptr;
+    const size_t n_ints = 4 + B + (bt.status ? 0 : B);
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scr), n_ints * sizeof(int32_t), st);
+    if (e != cudaSuccess) return set_error(PSR_E_OOM, "scratch allocation failed");
+    int32_t *q0 = scr, *q1 = scr + 1, *len = scr + 2, *list = scr + 4;
+    Batch b1 = bt;
+    if (!bt.status) b1.status = scr + 4 + B;
+    int rc = launch_solve_q<float>(m, b1, o, wpb_req, bps_req, st, q0);
+    if (rc == PSR_OK) {
+        cudaMemsetAsync(len, 0, sizeof(int32_t), st);
+        collect_unconverged<<<unsigned((B + 255) / 256), 256, 0, st>>>(bt.B, b1.status, list, len);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_error("collect_unconverged launch", e);
+    }
+    if (rc == PSR_OK) {
+        Batch b2 = b1;
+        b2.list = list;
+        b2.list_len = len;
+        b2.fallback = 1;
+        rc = launch_solve_q<double>(m, b2, o, wpb_req, bps_req, st, q1);
+    }
+    cudaFreeAsync(scr, st);
+    return rc;
+}
+
+template <class TJ>
 int launch_eval(const Mech &m, const Batch &bt, int energy, int want_J, double *out, cudaStream_t st) {
-    const size_t wsb = ws_bytes<TJ>(m.K, m.I, m.K + 1, m.n_troe);
+    const size_t wsb = ws_bytes<TJ>(m.K, m.I, m.K + 1 + m.dev.nsoot, m.n_troe, m.dev.nsoot);
     const int wpb = 2;
     const size_t smem = wpb * wsb;
     cudaError_t e = cudaFuncSetAttribute(eval_kernel<TJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -1251,7 +1445,7 @@ int launch_solve_noalloc(const Mech &m, const Batch &bt, const Opts &o, int wpb_
     int32_t *queue = nullptr;
     int rc = noalloc_scratch(&queue);
     if (rc != PSR_OK) return rc;
-    const size_t wsb = ws_bytes<TJ>(m.K, m.I, m.K + 1, m.n_troe);
+    const size_t wsb = ws_bytes<TJ>(m.K, m.I, m.K + 1 + m.dev.nsoot, m.n_troe, m.dev.nsoot);
     int dev = 0;
     cudaGetDevice(&dev);
     int max_smem = 0, nsm = 0;
@@ -1280,10 +1474,16 @@ int launch_solve_noalloc(const Mech &m, const Batch &bt, const Opts &o, int wpb_
     return PSR_OK;
 }
 
+// Mechanisms with at most 64 unknowns run on the warp-per-reactor kernels, larger gas
+// mechanisms on the block-per-reactor kernels (psr_block.cu).
+bool warp_path(const psr_mech *m) { return m->m.K + 1 + m->m.dev.nsoot <= kMaxWarpN; }
+
 int check_mech(const psr_mech *m) {
     if (!m) return set_error(PSR_E_ARG, "mechanism is NULL");
-    if (m->m.K + 1 > kMaxWarpN)
-        return set_error(PSR_E_UNSUPPORTED, "this kernel handles K + 1 <= 64 species unknowns");
+    if (!warp_path(m)) {
+        const int rc = block_check(m->m);
+        if (rc) return rc;
+    }
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != m->m.device) return set_error(PSR_E_ARG, "mechanism was loaded on another CUDA device");
@@ -1303,6 +1503,8 @@ int psr_batch_solve(const psr_mech *m, int64_t B, const double *Y_in, const doub
                     int32_t *nfev, const psr_options *opt, void *cuda_stream) {
     int rc = check_mech(m);
     if (rc) return rc;
+    if (m->m.has_soot)
+        return set_error(PSR_E_ARG, "mechanism carries soot: use the _soot entry points");
     if (B < 0) return set_error(PSR_E_ARG, "B < 0");
     if (B == 0) return PSR_OK;
     if (B > (int64_t(1) << 31) - 64) return set_error(PSR_E_ARG, "B too large");
@@ -1315,7 +1517,10 @@ int psr_batch_solve(const psr_mech *m, int64_t B, const double *Y_in, const doub
     psr_options_default(&d);
     const psr_options &po = opt ? *opt : d;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    if (po.precision == PSR_MIXED) return launch_solve<float>(m->m, bt, o, po.warps_per_block, po.blocks_per_sm, st);
+    if (!warp_path(m))
+        return block_solve(m->m, bt, o, po.precision, po.mixed_fallback != 0, po.blocks_per_sm, st);
+    if (po.precision == PSR_MIXED)
+        return launch_mixed(m->m, bt, o, po.warps_per_block, po.blocks_per_sm, po.mixed_fallback != 0, st);
     return launch_solve<double>(m->m, bt, o, po.warps_per_block, po.blocks_per_sm, st);
 }
 
@@ -1325,6 +1530,10 @@ int psr_batch_solve_noalloc(const psr_mech *m, int64_t B, const double *Y_in, co
                             double *fnorm, int32_t *nfev, const psr_options *opt, void *cuda_stream) {
     int rc = check_mech(m);
     if (rc) return rc;
+    if (m->m.has_soot)
+        return set_error(PSR_E_ARG, "mechanism carries soot: use the _soot entry points");
+    if (!warp_path(m))
+        return set_error(PSR_E_UNSUPPORTED, "psr_batch_solve_noalloc: at most 64 unknowns (K + 1)");
     if (B < 0) return set_error(PSR_E_ARG, "B < 0");
     if (B > kNoAllocMaxB)
         return set_error(PSR_E_ARG, "psr_batch_solve_noalloc: B exceeds the static work-queue limit of " +
@@ -1342,6 +1551,65 @@ int psr_batch_solve_noalloc(const psr_mech *m, int64_t B, const double *Y_in, co
     if (po.precision == PSR_MIXED)
         return launch_solve_noalloc<float>(m->m, bt, o, po.warps_per_block, po.blocks_per_sm, st);
     return launch_solve_noalloc<double>(m->m, bt, o, po.warps_per_block, po.blocks_per_sm, st);
+}
+
+int psr_batch_solve_soot(const psr_mech *m, int64_t B, const double *Y_in, const double *T_in, const double *tau,
+                         const double *P, const double *M_in, const double *Y0, const double *T0, const double *M0,
+                         const double *rate_mult, double *Y_out, double *T_out, double *M_out, int32_t *iters,
+                         int32_t *ts_steps, int32_t *status, double *fnorm, int32_t *nfev, const psr_options *opt,
+                         void *cuda_stream) {
+    int rc = check_mech(m);
+    if (rc) return rc;
+    if (!m->m.has_soot) return set_error(PSR_E_ARG, "mechanism has no soot record: use psr_batch_solve");
+    if (B < 0) return set_error(PSR_E_ARG, "B < 0");
+    if (B == 0) return PSR_OK;
+    if (B > (int64_t(1) << 31) - 64) return set_error(PSR_E_ARG, "B too large");
+    if (!Y_in || !T_in || !tau || !P || !M_in || !Y0 || !T0 || !Y_out || !T_out || !M_out)
+        return set_error(PSR_E_ARG, "psr_batch_solve_soot: required pointer is NULL");
+    if ((rc = check_opts(opt))) return rc;
+    Batch bt{B, Y_in, T_in, tau, P, Y0, T0, rate_mult, Y_out, T_out, fnorm, iters, ts_steps, status, nfev,
+             M_in, M0, M_out};
+    const Opts o = to_opts(opt);
+    psr_options d;
+    psr_options_default(&d);
+    const psr_options &po = opt ? *opt : d;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (po.precision == PSR_MIXED)
+        return launch_mixed(m->m, bt, o, po.warps_per_block, po.blocks_per_sm, po.mixed_fallback != 0, st);
+    return launch_solve<double>(m->m, bt, o, po.warps_per_block, po.blocks_per_sm, st);
+}
+
+int psr_eval_residual_soot(const psr_mech *m, int64_t B, const double *Y_in, const double *T_in, const double *tau,
+                           const double *P, const double *M_in, const double *Y, const double *T, const double *Mom,
+                           const double *rate_mult, double *F_out, int32_t energy, void *cuda_stream) {
+    int rc = check_mech(m);
+    if (rc) return rc;
+    if (!m->m.has_soot) return set_error(PSR_E_ARG, "mechanism has no soot record");
+    if (B < 0 || (energy != PSR_ADIABATIC && energy != PSR_FIXED_T)) return set_error(PSR_E_ARG, "bad B or energy");
+    if (B == 0) return PSR_OK;
+    if (!Y_in || !T_in || !tau || !P || !M_in || !Y || !T || !Mom || !F_out) return set_error(PSR_E_ARG, "NULL pointer");
+    Batch bt{B, Y_in, T_in, tau, P, Y, T, rate_mult, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+             M_in, Mom, nullptr};
+    return launch_eval<double>(m->m, bt, energy, 0, F_out, static_cast<cudaStream_t>(cuda_stream));
+}
+
+int psr_eval_jacobian_soot(const psr_mech *m, int64_t B, const double *Y_in, const double *T_in, const double *tau,
+                           const double *P, const double *M_in, const double *Y, const double *T, const double *Mom,
+                           const double *rate_mult, double *J_out, int32_t energy, int32_t precision,
+                           void *cuda_stream) {
+    int rc = check_mech(m);
+    if (rc) return rc;
+    if (!m->m.has_soot) return set_error(PSR_E_ARG, "mechanism has no soot record");
+    if (B < 0 || (energy != PSR_ADIABATIC && energy != PSR_FIXED_T) ||
+        (precision != PSR_FP64 && precision != PSR_MIXED))
+        return set_error(PSR_E_ARG, "bad B, energy or precision");
+    if (B == 0) return PSR_OK;
+    if (!Y_in || !T_in || !tau || !P || !M_in || !Y || !T || !Mom || !J_out) return set_error(PSR_E_ARG, "NULL pointer");
+    Batch bt{B, Y_in, T_in, tau, P, Y, T, rate_mult, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+             M_in, Mom, nullptr};
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (precision == PSR_MIXED) return launch_eval<float>(m->m, bt, energy, 1, J_out, st);
+    return launch_eval<double>(m->m, bt, energy, 1, J_out, st);
 }
 
 int psr_batch_solve_host(const psr_mech *m, int64_t B, const double *Y_in, const double *T_in, const double *tau,
@@ -1399,10 +1667,13 @@ int psr_eval_residual(const psr_mech *m, int64_t B, const double *Y_in, const do
                       int32_t energy, void *cuda_stream) {
     int rc = check_mech(m);
     if (rc) return rc;
+    if (m->m.has_soot)
+        return set_error(PSR_E_ARG, "mechanism carries soot: use the _soot entry points");
     if (B < 0 || (energy != PSR_ADIABATIC && energy != PSR_FIXED_T)) return set_error(PSR_E_ARG, "bad B or energy");
     if (B == 0) return PSR_OK;
     if (!Y_in || !T_in || !tau || !P || !Y || !T || !F_out) return set_error(PSR_E_ARG, "NULL pointer");
     Batch bt{B, Y_in, T_in, tau, P, Y, T, rate_mult, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (!warp_path(m)) return block_eval(m->m, bt, energy, 0, PSR_FP64, F_out, static_cast<cudaStream_t>(cuda_stream));
     return launch_eval<double>(m->m, bt, energy, 0, F_out, static_cast<cudaStream_t>(cuda_stream));
 }
 
@@ -1411,6 +1682,8 @@ int psr_eval_jacobian(const psr_mech *m, int64_t B, const double *Y_in, const do
                       int32_t energy, int32_t precision, void *cuda_stream) {
     int rc = check_mech(m);
     if (rc) return rc;
+    if (m->m.has_soot)
+        return set_error(PSR_E_ARG, "mechanism carries soot: use the _soot entry points");
     if (B < 0 || (energy != PSR_ADIABATIC && energy != PSR_FIXED_T) ||
         (precision != PSR_FP64 && precision != PSR_MIXED))
         return set_error(PSR_E_ARG, "bad B, energy or precision");
@@ -1418,6 +1691,7 @@ int psr_eval_jacobian(const psr_mech *m, int64_t B, const double *Y_in, const do
     if (!Y_in || !T_in || !tau || !P || !Y || !T || !J_out) return set_error(PSR_E_ARG, "NULL pointer");
     Batch bt{B, Y_in, T_in, tau, P, Y, T, rate_mult, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (!warp_path(m)) return block_eval(m->m, bt, energy, 1, precision, J_out, st);
     if (precision == PSR_MIXED) return launch_eval<float>(m->m, bt, energy, 1, J_out, st);
     return launch_eval<double>(m->m, bt, energy, 1, J_out, st);
 }
@@ -1427,11 +1701,15 @@ int psr_batch_adjoint(const psr_mech *m, int64_t B, const double *Y_in, const do
                       double *grad_out, double *lambda_out, int32_t *ok_out, int32_t energy, void *cuda_stream) {
     int rc = check_mech(m);
     if (rc) return rc;
+    if (m->m.has_soot)
+        return set_error(PSR_E_ARG, "mechanism carries soot: use the _soot entry points");
     if (B < 0 || (energy != PSR_ADIABATIC && energy != PSR_FIXED_T)) return set_error(PSR_E_ARG, "bad B or energy");
     if (B == 0) return PSR_OK;
     if (!Y_in || !T_in || !tau || !P || !Y || !T || !g || !grad_out)
         return set_error(PSR_E_ARG, "psr_batch_adjoint: required pointer is NULL");
     Batch bt{B, Y_in, T_in, tau, P, Y, T, rate_mult, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (!warp_path(m))
+        return block_adjoint(m->m, bt, energy, g, grad_out, lambda_out, ok_out, static_cast<cudaStream_t>(cuda_stream));
     const Mech &mm = m->m;
     const size_t wsb = ws_bytes<double>(mm.K, mm.I, mm.K + 1, mm.n_troe);
     const int wpb = 2;
@@ -1448,11 +1726,12 @@ int psr_batch_adjoint(const psr_mech *m, int64_t B, const double *Y_in, const do
 
 int psr_batch_lu_solve(int64_t B, int32_t n, const double *A, const double *r, double *x_out, int32_t *ok_out,
                        int32_t precision, void *cuda_stream) {
-    if (B < 0 || n < 1 || n > kMaxWarpN || (precision != PSR_FP64 && precision != PSR_MIXED))
+    if (B < 0 || n < 1 || n > 512 || (precision != PSR_FP64 && precision != PSR_MIXED))
         return set_error(PSR_E_ARG, "psr_batch_lu_solve: bad B, n or precision");
     if (B == 0) return PSR_OK;
     if (!A || !r || !x_out || !ok_out) return set_error(PSR_E_ARG, "psr_batch_lu_solve: NULL pointer");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (n > kMaxWarpN) return block_lu(B, n, A, r, x_out, ok_out, precision, st);
     const int wpb = 4;
     const int64_t grid = (B + wpb - 1) / wpb;
     cudaError_t e;

@@ -16,7 +16,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpsr.so")
 
 PSR_OK = 0
-PSR_CONVERGED, PSR_MAX_ITER, PSR_NONFINITE, PSR_TS_EXHAUSTED = 0, 1, 2, 4
+PSR_CONVERGED, PSR_MAX_ITER, PSR_NONFINITE, PSR_TS_EXHAUSTED, PSR_REFINE_FALLBACK = 0, 1, 2, 4, 5
+CONVERGED_STATES = (PSR_CONVERGED, PSR_REFINE_FALLBACK)
 PSR_FP64, PSR_MIXED = 0, 1
 PSR_ADIABATIC, PSR_FIXED_T = 0, 1
 
@@ -43,7 +44,8 @@ class COptions(ctypes.Structure):
                 ("max_ts_rounds", ctypes.c_int32), ("ts_steps", ctypes.c_int32),
                 ("ts_newton", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("energy", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("blocks_per_sm", ctypes.c_int32), ("mixed_fallback", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 _lib = None
@@ -74,6 +76,9 @@ def lib():
         L.psr_eval_jacobian.argtypes = [vp, i64] + [dp] * 7 + [dp, i32, i32, vp]
         L.psr_batch_lu_solve.argtypes = [i64, i32, dp, dp, dp, dp, i32, vp]
         L.psr_batch_adjoint.argtypes = [vp, i64] + [dp] * 7 + [dp, dp, dp, dp, i32, vp]
+        L.psr_batch_solve_soot.argtypes = [vp, i64] + [dp] * 9 + [dp] * 3 + [dp] * 5 + [ctypes.POINTER(COptions), vp]
+        L.psr_eval_residual_soot.argtypes = [vp, i64] + [dp] * 9 + [dp, i32, vp]
+        L.psr_eval_jacobian_soot.argtypes = [vp, i64] + [dp] * 9 + [dp, i32, i32, vp]
         _lib = L
     return _lib
 
@@ -106,6 +111,7 @@ class Options:
     energy: int = PSR_ADIABATIC
     warps_per_block: int = 0
     blocks_per_sm: int = 0
+    mixed_fallback: int = 1
 
     def to_c(self):
         o = COptions()
@@ -300,3 +306,54 @@ def batch_adjoint(mech: Mechanism, Y_in, T_in, tau, P, Y, T, g, rate_mult=None, 
         _ptr(P, f64, (B,)), _ptr(Y, f64, (B, K)), _ptr(T, f64, (B,)), _ptr(rate_mult, f64, (mech.I,)),
         _ptr(g, f64, (B, K + 1), "g"), grad.data_ptr(), lam.data_ptr(), ok.data_ptr(), energy, _stream()))
     return grad, lam, ok
+
+
+def batch_solve_soot(mech: Mechanism, Y_in, T_in, tau, P, M_in, Y0, T0, M0=None, rate_mult=None,
+                     opts: Options = None, out=None):
+    """psr_batch_solve_soot on torch CUDA tensors (gas + six MOMIC moments). Returns the
+    batch_solve dict plus M [B, 6]."""
+    import torch
+    f64, i32 = torch.float64, torch.int32
+    B, K = Y_in.shape
+    dev = Y_in.device
+    if out is None:
+        out = dict(Y=torch.empty((B, K), dtype=f64, device=dev), T=torch.empty(B, dtype=f64, device=dev),
+                   M=torch.empty((B, 6), dtype=f64, device=dev),
+                   iters=torch.empty(B, dtype=i32, device=dev), ts_steps=torch.empty(B, dtype=i32, device=dev),
+                   status=torch.empty(B, dtype=i32, device=dev), fnorm=torch.empty(B, dtype=f64, device=dev),
+                   nfev=torch.empty(B, dtype=i32, device=dev))
+    o = (opts or Options()).to_c()
+    _check(lib().psr_batch_solve_soot(
+        mech.handle, B, _ptr(Y_in, f64, (B, K), "Y_in"), _ptr(T_in, f64, (B,), "T_in"),
+        _ptr(tau, f64, (B,), "tau"), _ptr(P, f64, (B,), "P"), _ptr(M_in, f64, (B, 6), "M_in"),
+        _ptr(Y0, f64, (B, K), "Y0"), _ptr(T0, f64, (B,), "T0"), _ptr(M0, f64, (B, 6), "M0"),
+        _ptr(rate_mult, f64, (mech.I,), "rate_mult"),
+        _ptr(out["Y"], f64, (B, K)), _ptr(out["T"], f64, (B,)), _ptr(out["M"], f64, (B, 6)),
+        _ptr(out["iters"], i32, (B,)), _ptr(out["ts_steps"], i32, (B,)), _ptr(out["status"], i32, (B,)),
+        _ptr(out["fnorm"], f64, (B,)), _ptr(out["nfev"], i32, (B,)), ctypes.byref(o), _stream()))
+    return out
+
+
+def eval_residual_soot(mech: Mechanism, Y_in, T_in, tau, P, M_in, Y, T, M, rate_mult=None, energy=PSR_ADIABATIC):
+    import torch
+    f64 = torch.float64
+    B, K = Y.shape
+    F = torch.empty((B, K + 7), dtype=f64, device=Y.device)
+    _check(lib().psr_eval_residual_soot(
+        mech.handle, B, _ptr(Y_in, f64, (B, K)), _ptr(T_in, f64, (B,)), _ptr(tau, f64, (B,)), _ptr(P, f64, (B,)),
+        _ptr(M_in, f64, (B, 6)), _ptr(Y, f64, (B, K)), _ptr(T, f64, (B,)), _ptr(M, f64, (B, 6)),
+        _ptr(rate_mult, f64, (mech.I,)), F.data_ptr(), energy, _stream()))
+    return F
+
+
+def eval_jacobian_soot(mech: Mechanism, Y_in, T_in, tau, P, M_in, Y, T, M, rate_mult=None, energy=PSR_ADIABATIC,
+                       precision=PSR_FP64):
+    import torch
+    f64 = torch.float64
+    B, K = Y.shape
+    J = torch.empty((B, K + 7, K + 7), dtype=f64, device=Y.device)
+    _check(lib().psr_eval_jacobian_soot(
+        mech.handle, B, _ptr(Y_in, f64, (B, K)), _ptr(T_in, f64, (B,)), _ptr(tau, f64, (B,)), _ptr(P, f64, (B,)),
+        _ptr(M_in, f64, (B, 6)), _ptr(Y, f64, (B, K)), _ptr(T, f64, (B,)), _ptr(M, f64, (B, 6)),
+        _ptr(rate_mult, f64, (mech.I,)), J.data_ptr(), energy, precision, _stream()))
+    return J

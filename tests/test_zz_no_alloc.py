@@ -50,7 +50,8 @@ def test_noalloc_matches_allocating_entry(dev, precision):
     batch = synth.workload_batch("k10_b64", spec)
     t = {k: torch.tensor(getattr(batch, k), dtype=torch.float64, device=dev)
          for k in ("Y_in", "T_in", "tau", "P", "Y0", "T0")}
-    opts = psr.Options(precision=precision).to_c()
+    # the allocating entry without its FP64 fallback is the single launch this entry runs
+    opts = psr.Options(precision=precision, mixed_fallback=0).to_c()
     L = psr.lib()
     ref = _outputs(torch, batch.B, spec.K, dev)
     _call(L.psr_batch_solve, mech, t, ref, opts, torch)
