@@ -30,6 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "k53_b4096"
+MIXED = "mixed_b32768"       # the uneven batch: 50/35/15 % of K = 10 / 53 / 200 reactors
 METRIC = "converged PSR solves/s, mixed vs FP64 form on one GB300 at ‖F‖∞≤1e-8; roofline %"
 UNIT = "solves/s"
 FP64_PEAK_TFLOPS = 1.25          # nominal GB300 FP64 (non-tensor) rate
@@ -70,6 +71,14 @@ def fp64_work(mech_spec, nfev, iters, precision):
     W_F = (K * 45 + I * (20 + 2 * EXP_FLOPS) + 2 * n_eff + 2 * nnz + K * 4
            + n_troe * (4 * EXP_FLOPS + 2 * LOG_FLOPS + 30) + 2 * LOG_FLOPS + 4 * DIV_FLOPS)
     W_J = I * 80 + 4 * nnz + 2 * K * K + 4 * K * K + (n_tb + n_troe) * 12 + n_troe * (60 + 4 * EXP_FLOPS + 2 * LOG_FLOPS)
+    if mech_spec.soot is not None:
+        # one MOMIC source evaluation: 29 fractional moments (exp), 28 grid-function logs,
+        # 7 interpolated f(1/2) (exp) and the nucleation/growth rates; the Jacobian's soot
+        # block takes 17 of them plus 9 (K + 7) chained entries
+        n = K + 7
+        W_S_EVAL = 36 * EXP_FLOPS + 30 * LOG_FLOPS + 400
+        W_F += W_S_EVAL + 6 * (EXP_FLOPS + 10)
+        W_J += 17 * W_S_EVAL + 9 * n * 12
     W_LU = 2.0 * n ** 3 / 3.0 if precision == "fp64" else 0.0
     W_S = 2.0 * n * n if precision == "fp64" else 0.0
     nf, it = float(np.sum(nfev)), float(np.sum(iters))
@@ -133,16 +142,52 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------- oracle timing
+def oracle_sample_size(spec):
+    """Reactors the oracle solves for the CPU baseline: about 10-30 s of one core."""
+    return 6 if spec.K <= 60 else 1
+
+
 def oracle_time(name, indices):
+    """Converged count and seconds of the oracle on reactors `indices` of a workload
+    (gas, or gas + MOMIC soot for a sooting mechanism)."""
+    import warnings
     from oracle import psr_oracle as O
     from paper_2005_11468_gb300 import synth
+    warnings.filterwarnings("ignore", category=RuntimeWarning)   # trial states of the damped Newton
     spec = synth.workload_mechanism(name)
     mech = O.Mechanism(synth.mechanism_text(spec))
     batch = synth.workload_batch(name, spec)
     t0 = time.perf_counter()
-    res = O.solve_batch(mech, batch, indices=list(indices))
-    dt = time.perf_counter() - t0
-    return int(np.sum(res["status"] == O.CONVERGED)), dt
+    if spec.soot is not None:
+        from oracle import momic_oracle as S
+        conv = 0
+        for b in indices:
+            r, _ = S.solve_soot_reactor(mech, O.inlet_of(batch, b), batch.Y0[b], batch.T0[b], batch.M_in[b])
+            conv += int(r.status == O.CONVERGED)
+    else:
+        res = O.solve_batch(mech, batch, indices=list(indices))
+        conv = int(np.sum(res["status"] == O.CONVERGED))
+    return conv, time.perf_counter() - t0
+
+
+def oracle_time_mixed(per_class):
+    """Oracle seconds per reactor of the uneven batch: `per_class` reactors of each
+    mechanism class timed, weighted by the class fractions. Returns (solves/s, detail)."""
+    from oracle import psr_oracle as O
+    from paper_2005_11468_gb300 import synth
+    specs = [synth.workload_mechanism(nm) for nm in synth.MIXED_WORKLOAD["parts"]]
+    mb = synth.mixed_batch(specs, B=512)
+    t_avg, conv_frac, detail = 0.0, 0.0, []
+    for c, (spec, frac, n) in enumerate(zip(specs, synth.MIXED_WORKLOAD["fractions"], per_class)):
+        mech = O.Mechanism(synth.mechanism_text(spec))
+        bc = mb["batches"][c]
+        t0 = time.perf_counter()
+        res = O.solve_batch(mech, bc, indices=list(range(n)))
+        dt = (time.perf_counter() - t0) / n
+        t_avg += frac * dt
+        conv_frac += frac * float(np.mean(res["status"] == O.CONVERGED))
+        detail.append(f"{n} K={spec.K} reactors {dt:.2f} s each")
+    return conv_frac / t_avg, "; ".join(detail)
 
 
 def run_reference(args):
@@ -150,6 +195,16 @@ def run_reference(args):
     if rank != 0:
         return
     K, W = args.steps, args.warmup
+    if args.workload == MIXED:
+        v, detail = oracle_time_mixed((2, 1, 1))
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": K, "warmup": W, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"{MIXED} (class-weighted oracle sample)"},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": detail},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
     conv_total, t_total = 0, 0.0
     for s in range(W + K):
         c, dt = oracle_time(args.workload, [s])
@@ -298,7 +353,8 @@ def run_ours(args):
         "ms_per_step": avg_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64 residual / f32 Jacobian+LU", "data": "synthetic",
         "config": {"workload": f"{args.workload}: K={spec.K} species, I={spec.I} reactions "
-                               f"(10 third-body, 15 Troe), B={B} reactors per GPU, adiabatic, 1 atm",
+                               f"({spec.n_tb} third-body, {spec.n_troe} Troe), B={B} reactors per GPU, "
+                               f"adiabatic, 1 atm",
                    "global_batch": B * world, "precision": "mixed", "parallelism": f"dp{world} (independent reactors)",
                    "l2": "flushed (256 MB write) between timed steps"},
         "fp64_form": {"value": value64, "unit": UNIT, "ms_per_step": fp64["total_ms"] / len(fp64["ms"]),
@@ -311,14 +367,16 @@ def run_ours(args):
                      "peak_source": "nominal GB300 FP64 rate (recipe table); measured FMA loop 1.198",
                      "work_model": "FP64 flops with exp=40, log=73, div=16 flop slots"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": K,
+        # per step: the FP32-Jacobian solve, the unconverged-list kernel, the FP64 re-solve
+        "gpu_launches": 3 * K,
         "clocks": sampler.summary(),
     }
     if not args.no_cpu_baseline:
-        idx = list(range(6))
+        n_cpu = oracle_sample_size(spec)
+        idx = list(range(n_cpu))
         c, dt = oracle_time(args.workload, idx)
         line["cpu_baseline"] = {"value": c / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"reactors 0..5 of {args.workload} ({c} converged, {dt:.1f} s)"}
+                                "sample": f"reactors 0..{n_cpu - 1} of {args.workload} ({c} converged, {dt:.1f} s)"}
     print(json.dumps(line))
     if pg is not None:
         pg.destroy_process_group()
@@ -352,6 +410,8 @@ def run_soot_tail(args, spec, batch, mixed, fp64, t, solve, flush, barrier, pg, 
     value64 = conv64 / (fp64["total_ms"] / 1e3)
     if rank != 0:
         return
+    avg_ms = mixed["total_ms"] / K
+    achieved = fp64_work(spec, mixed["nfev"], mixed["iters"], "mixed") / (avg_ms / 1e3) / 1e12
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": mixed["total_ms"] / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 residual / f32 Jacobian+LU", "data": "synthetic",
@@ -362,8 +422,17 @@ def run_soot_tail(args, spec, batch, mixed, fp64, t, solve, flush, barrier, pg, 
             "mixed_vs_fp64": value / value64 if value64 > 0 else None,
             "converged_fraction": mixed["conv"] / B,
             "newton_iters_median": float(np.median(mixed["iters"])),
+            "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "peak_source": "nominal GB300 FP64 rate (recipe table); measured FMA loop 1.198",
+                         "work_model": "FP64 flops with exp=40, log=73, div=16 flop slots, MOMIC terms"},
             "e2e": {"value": e_conv / e_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": K, "clocks": sampler.summary()}
+            "gpu_launches": 3 * K, "clocks": sampler.summary()}
+    if not args.no_cpu_baseline:
+        n_cpu = 2
+        c, dt = oracle_time(args.workload, list(range(n_cpu)))
+        line["cpu_baseline"] = {"value": c / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"reactors 0..{n_cpu - 1} of {args.workload} ({c} converged, {dt:.1f} s)"}
     print(json.dumps(line))
 
 
@@ -375,10 +444,153 @@ class _Null:
         return False
 
 
+def run_multi(args):
+    """The uneven batch through psr_batch_solve_multi, captured once in a CUDA graph and
+    replayed per step (mixed form); the FP64 form by direct calls; e2e through the call
+    with the packed inputs copied from pinned host memory and the results read back."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    from paper_2005_11468_gb300 import _build, psr, synth
+    if not os.path.exists(psr.LIB_PATH):
+        _build.build()
+    specs = [synth.workload_mechanism(nm) for nm in synth.MIXED_WORKLOAD["parts"]]
+    gms = [psr.Mechanism(synth.mechanism_text(sp)) for sp in specs]
+    mb = synth.mixed_batch(specs, seed=synth.MECH_SEED_BASE + 10 * synth.MIXED_WORKLOAD["tag"] + 1 + 1000 * rank)
+    B = len(mb["mech_id"])
+    keys = ("Y_in", "Y0", "T_in", "tau", "P", "T0")
+    host = {k: torch.tensor(mb[k], dtype=torch.float64).pin_memory() for k in keys}
+    host["mech_id"] = torch.tensor(mb["mech_id"], dtype=torch.int32).pin_memory()
+    host["row_off"] = torch.tensor(mb["row_off"], dtype=torch.int64).pin_memory()
+    t = {k: v.to(dev) for k, v in host.items()}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    K, W = args.steps, args.warmup
+
+    def call(opts, out=None):
+        return psr.batch_solve_multi(gms, t["mech_id"], t["row_off"], t["Y_in"], t["T_in"], t["tau"], t["P"],
+                                     t["Y0"], t["T0"], opts=opts, out=out)
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    mixed_opts = psr.Options(precision=psr.PSR_MIXED)
+    out = None
+    for _ in range(W):
+        out = call(mixed_opts, out)
+    barrier()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        call(mixed_opts, out)
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, capture_error_mode="thread_local"):
+        call(mixed_opts, out)
+    barrier()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    sampler = ClockSampler(local)
+    with sampler:
+        for s in range(K):
+            flush.fill_(float(s))
+            ev[s][0].record(stream)
+            graph.replay()
+            ev[s][1].record(stream)
+        barrier()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    st = out["status"].cpu().numpy()
+    nfev, iters = out["nfev"].cpu().numpy(), out["iters"].cpu().numpy()
+    conv = int(np.isin(st, psr.CONVERGED_STATES).sum())
+    # FP64 form, direct calls
+    fp64_opts = psr.Options(precision=psr.PSR_FP64)
+    o64 = call(fp64_opts)
+    barrier()
+    n64 = max(1, min(K, 2))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n64):
+        call(fp64_opts, o64)
+    e1.record(stream)
+    barrier()
+    ms64 = e0.elapsed_time(e1) / n64
+    conv64 = int(np.isin(o64["status"].cpu().numpy(), psr.CONVERGED_STATES).sum())
+    # end to end: pinned host -> device, the call, results -> host
+    hout = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
+    e_conv, e_t = 0, 0.0
+    for s in range(K):
+        flush.fill_(float(s))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k, v in host.items():
+            t[k].copy_(v, non_blocking=True)
+        o = call(mixed_opts, out)
+        for k in ("Y", "T", "status"):
+            hout[k].copy_(o[k], non_blocking=True)
+        torch.cuda.synchronize()
+        e_t += time.perf_counter() - t0
+        e_conv += int(np.isin(hout["status"].numpy(), psr.CONVERGED_STATES).sum())
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = sum(hout[k].numel() * hout[k].element_size() for k in ("Y", "T", "status"))
+    total = sum(ms)
+    vals = torch.tensor([conv * K, total, conv64, ms64, e_conv, e_t], dtype=torch.float64, device=dev)
+    if pg is not None:
+        mx = vals.clone()
+        pg.all_reduce(mx, op=pg.ReduceOp.MAX)
+        pg.all_reduce(vals)
+        vals[1], vals[3], vals[5] = mx[1], mx[3], mx[5]
+    conv_all, total, conv64_all, ms64, e_conv, e_t = vals.tolist()
+    if rank != 0:
+        if pg is not None:
+            pg.destroy_process_group()
+        return
+    value = conv_all / (total / 1e3)
+    value64 = conv64_all / (ms64 / 1e3)
+    work = sum(fp64_work(sp, nfev[mb["members"][c]], iters[mb["members"][c]], "mixed") for c, sp in enumerate(specs))
+    achieved = work / (total / K / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 residual / f32 Jacobian+LU", "data": "synthetic",
+        "config": {"workload": f"{MIXED}: {B} reactors per GPU, 50/35/15 % of K=10/53/200 mechanisms "
+                               f"(I=24/325/1500), shuffled, one psr_batch_solve_multi call replayed as a CUDA graph",
+                   "global_batch": B * world, "precision": "mixed", "parallelism": f"dp{world} (independent reactors)",
+                   "l2": "flushed (256 MB write) between timed steps"},
+        "fp64_form": {"value": value64, "unit": UNIT, "ms_per_step": ms64, "converged": int(conv64)},
+        "mixed_vs_fp64": value / value64 if value64 > 0 else None,
+        "converged_fraction": conv / B,
+        "newton_iters_median": float(np.median(iters)),
+        "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "nominal GB300 FP64 rate (recipe table); measured FMA loop 1.198",
+                     "work_model": "FP64 flops with exp=40, log=73, div=16 flop slots, summed over classes"},
+        "e2e": {"value": e_conv / e_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        # per step: bucketing, and per class the solver, the unconverged list and the FP64 re-solve
+        "gpu_launches": K * (1 + 3 * len(specs)),
+        "clocks": sampler.summary(),
+    }
+    if not args.no_cpu_baseline:
+        v, detail = oracle_time_mixed((2, 1, 1))
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"class-weighted: {detail}"}
+    print(json.dumps(line))
+    if pg is not None:
+        pg.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == MIXED:
+        run_multi(args)
     else:
         run_ours(args)
 

@@ -47,6 +47,7 @@ extern "C" {
 #define PSR_MAX_ITER 1      /* max_newton Newton iterations used */
 #define PSR_NONFINITE 2     /* the residual at the initial guess is not finite */
 #define PSR_TS_EXHAUSTED 4  /* max_ts_rounds time-stepping rounds, or dt collapsed */
+#define PSR_BAD_INPUT 7      /* psr_batch_solve_multi: mechanism id out of range, not solved */
 #define PSR_REFINE_FALLBACK 5 /* PSR_MIXED: converged (same criterion) after the FP32-Jacobian
                                  launch left it unconverged and the FP64 re-solve succeeded */
 
@@ -179,6 +180,29 @@ int psr_eval_jacobian_soot(const psr_mech *m, int64_t B,
                            const double *M_in, const double *Y, const double *T, const double *M,
                            const double *rate_mult, double *J_out, int32_t energy, int32_t precision,
                            void *cuda_stream);
+
+/* Uneven batch: B reactors of up to 8 gas mechanisms (different K) in one call, e.g. a
+ * mix of small and large mechanisms as a reacting-flow code hands them over (the paper's
+ * batch of independent PSRs, Sec. 6). mech_id [B] (device, int32) picks mechs[mech_id[r]];
+ * row_off [B] (device, int64) is the offset of reactor r's row in the packed arrays
+ * Y_in, Y0 and Y_out (row r holds K of its mechanism); T_in, tau, P, T0, T_out and the
+ * per-reactor outputs are [B] as in psr_batch_solve. No rate multipliers. A device
+ * kernel buckets the reactors by mechanism; each mechanism's persistent solver (warp per
+ * reactor for K + 1 <= 64, block per reactor above) then runs on its own library-owned
+ * stream forked from and joined back to cuda_stream, largest K first, so the launches
+ * overlap. The call can be captured into a CUDA graph (all work joins back into
+ * cuda_stream); concurrent callers on one device serialise on a mutex while enqueueing.
+ * A reactor whose mech_id is out of range gets status PSR_BAD_INPUT (status scratch is
+ * allocated when status is NULL) and is otherwise untouched.
+ * Device memory: scratch lists, 4 (8 + (n_mech + 1) B) bytes, allocated on the stream.
+ * Errors: PSR_E_ARG (n_mech outside 1..8, NULL, soot mechanism), PSR_E_UNSUPPORTED,
+ * PSR_E_CUDA. */
+int psr_batch_solve_multi(const psr_mech *const *mechs, int32_t n_mech, int64_t B,
+                          const int32_t *mech_id, const int64_t *row_off,
+                          const double *Y_in, const double *T_in, const double *tau, const double *P,
+                          const double *Y0, const double *T0, double *Y_out, double *T_out,
+                          int32_t *iters, int32_t *ts_steps, int32_t *status, double *fnorm,
+                          int32_t *nfev, const psr_options *opt, void *cuda_stream);
 
 /* Same as psr_batch_solve with every array in HOST memory: the call copies the inputs
  * to the device, solves, copies the outputs back and synchronises the stream before

@@ -363,11 +363,15 @@ int upload(Mech &m) {
     std::vector<char> blob;
     std::vector<double> invW(m.K);
     for (int k = 0; k < m.K; ++k) invW[k] = 1.0 / m.W[k];
+    std::vector<float> invW_f(invW.begin(), invW.end()), eff_val_f(m.eff_val.begin(), m.eff_val.end());
+    size_t oinvWf, oeffvf;
     size_t oW, oinvW, onasa, olnA, obeta, otheta, oslots, odnu, otype, oeffp, oeffs, oeffv, otr, otroe,
         osp, ospr, ospn, opart, opartnu, opfm, oprm, oorig, odnud, ospnd, osoot;
     std::vector<double> dnu_d(m.dnu.begin(), m.dnu.end()), sp_nu_d(m.sp_nu.begin(), m.sp_nu.end());
     place(blob, m.W, oW);
     place(blob, invW, oinvW);
+    place(blob, invW_f, oinvWf);
+    place(blob, eff_val_f, oeffvf);
     place(blob, m.nasa, onasa);
     place(blob, m.lnA, olnA);
     place(blob, m.beta, obeta);
@@ -412,6 +416,8 @@ int upload(Mech &m) {
     D.n_eff = static_cast<int>(m.eff_sp.size());
     D.W = reinterpret_cast<const double *>(b + oW);
     D.invW = reinterpret_cast<const double *>(b + oinvW);
+    D.invW_f = reinterpret_cast<const float *>(b + oinvWf);
+    D.eff_val_f = reinterpret_cast<const float *>(b + oeffvf);
     D.nasa = reinterpret_cast<const double *>(b + onasa);
     D.lnA = reinterpret_cast<const double *>(b + olnA);
     D.beta = reinterpret_cast<const double *>(b + obeta);

@@ -33,7 +33,7 @@ struct BWS {
     double *v, *ra, *rb;      // [K] wdot / dense third-body column part; row coefficients
     double *tD, *tX;          // [n_troe] falloff derivative caches
     double *red;              // [kRedSlots][kBW] reduction partials
-    int *ired;                // [kBW] pivot-search partials, then the work-queue slot
+    int *ired;                // [2][kBW] pivot-search partials (double-buffered), then the work-queue slot
     TJ *J;                    // [n][P]
     TJ *rhs;                  // [n]
     int16_t *perm;            // [n]
@@ -54,7 +54,7 @@ __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(
 template <class TJ>
 __host__ __device__ inline size_t bws_bytes(int K, int I, int nt, int n, bool j_in_smem) {
     size_t b = align16(sizeof(double) * bws_doubles(K, I, nt, n));
-    b = align16(b + sizeof(int) * (kBW + 4));
+    b = align16(b + sizeof(int) * (2 * kBW + 4));
     b = align16(b + sizeof(TJ) * n);
     b = align16(b + sizeof(int16_t) * n);
     if (j_in_smem) b = align16(b + sizeof(TJ) * size_t(n) * pitch_of(n));
@@ -96,7 +96,7 @@ __device__ BWS<TJ> bcarve(char *base, int K, int I, int nt, int n, TJ *Jglobal) 
     w.red = d;
     size_t off = align16(sizeof(double) * bws_doubles(K, I, nt, n));
     w.ired = reinterpret_cast<int *>(base + off);
-    off = align16(off + sizeof(int) * (kBW + 4));
+    off = align16(off + sizeof(int) * (2 * kBW + 4));
     w.rhs = reinterpret_cast<TJ *>(base + off);
     off = align16(off + sizeof(TJ) * n);
     w.perm = reinterpret_cast<int16_t *>(base + off);
@@ -360,7 +360,7 @@ __device__ void b_eval_J(const DevMech &M, const BWS<TJ> &w, const double *c, co
             if (typ != kElem) {
                 atomicAdd(w.v + pl[r], double(pnu[r]) * dqdM);
                 for (int e = __ldg(M.eff_ptr + i); e < __ldg(M.eff_ptr + i + 1); ++e)
-                    atomicAdd(row + __ldg(M.eff_sp + e), pnu[r] * dqdM_t * TJ(__ldg(M.eff_val + e)));
+                    atomicAdd(row + __ldg(M.eff_sp + e), pnu[r] * dqdM_t * eff_v<TJ>(M, e));
             }
         }
         w.q[i] = g;       // per-reaction Euler sum
@@ -381,6 +381,7 @@ __device__ void b_eval_J(const DevMech &M, const BWS<TJ> &w, const double *c, co
     double eJ = 0.0;
     if (energy != PSR_FIXED_T) {
         double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // Q, Sh, Hv, cw, hwT
+        if (t < K) w.rhs[t] = TJ(w.hRT[t]);          // H/RT in the Jacobian's precision (column sums)
         if (t < K) {
             const double H = w.hRT[t] * RT;
             acc[0] = H * wd;
@@ -395,7 +396,7 @@ __device__ void b_eval_J(const DevMech &M, const BWS<TJ> &w, const double *c, co
         const double inv_cpT = 1.0 / (cp * T);
         if (t < K) {
             TJ colsum = TJ(0);
-            for (int k = 0; k < K; ++k) colsum += TJ(w.hRT[k]) * w.J[size_t(k) * P + t];
+            for (int k = 0; k < K; ++k) colsum += w.rhs[k] * w.J[size_t(k) * P + t];
             const double cs = double(colsum) * RT + Hv;
             const double invWj = __ldg(M.invW + t);
             const double dN = tau * invWj * (cs + Wbar * (Q - Sh) / rho);
@@ -419,7 +420,7 @@ __device__ void b_eval_J(const DevMech &M, const BWS<TJ> &w, const double *c, co
         const TJ ak = TJ(w.ra[k]), bk = TJ(w.rb[k]), vkt = TJ(w.v[k]);
         TJ *row = w.J + size_t(k) * P;
         for (int j = lane; j < K; j += 32) {
-            const TJ invWj = TJ(__ldg(M.invW + j));
+            const TJ invWj = inv_w<TJ>(M, j);
             row[j] = (bk - ak * (row[j] + vkt)) * invWj + ((j == k) ? TJ(1) : TJ(0));
         }
     }
@@ -433,108 +434,247 @@ __device__ void b_eval_J(const DevMech &M, const BWS<TJ> &w, const double *c, co
 }
 
 // ---------------------------------------------------------------- LU (partial pivoting)
-// In-place LU of w.J with row interchanges (perm = final row order); rows below the pivot
-// are updated one warp per row, lanes over columns. False on a zero or non-finite pivot
-// (block-uniform).
+// Candidate for the next pivot: largest |a| by integer key, ties to the lower row (a NaN
+// ranks first and then fails the factorisation).
 template <class TJ>
-__device__ bool b_lu_factor(const BWS<TJ> &w, int n) {
+__device__ __forceinline__ void pivot_candidate(TJ v, int row, unsigned long long &best, TJ &bv, int &bi) {
+    const unsigned long long a = abs_key(v);
+    if (a > best || (a == best && row < bi)) {
+        best = a;
+        bv = v;
+        bi = row;
+    }
+}
+
+template <class TJ>
+__device__ __forceinline__ void warp_argmax(unsigned long long &best, TJ &bv, int &bi) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ob = __shfl_xor_sync(kFull, best, o);
+        const TJ ov = __shfl_xor_sync(kFull, bv, o);
+        const int oi = __shfl_xor_sync(kFull, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+            best = ob;
+            bv = ov;
+            bi = oi;
+        }
+    }
+}
+
+constexpr int kNB = 32;                  // panel width of the blocked LU
+constexpr int kTB = 4;                   // trailing-update tile per thread: rows w + 16 a (a < TA), columns l + 32 b
+template <class TJ>
+struct TileRows {
+    static constexpr int value = sizeof(TJ) == 8 ? 4 : 8;
+};
+
+// Blocked right-looking LU with partial pivoting (the LAPACK getrf order: panel,
+// row interchanges, triangular solve for the U block row, rank-32 trailing update), in
+// place in w.J; perm = final row order. The panel is factored column by column with one
+// thread per row (two block barriers per column: pivot offers, then the interchange);
+// U12 = L11^-1 A12 takes one thread per column; A22 -= L21 U12 runs as a register-tiled
+// product (8 x 4 outputs per thread, 12 shared loads per 32 FMAs). False on a zero or
+// non-finite pivot (block-uniform).
+template <class TJ>
+__device__ __noinline__ bool b_lu(const BWS<TJ> &w, int n) {
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const int P = w.P;
+    TJ *J = w.J;
+    unsigned long long *ckey = reinterpret_cast<unsigned long long *>(w.red);   // [2][kBW] pivot offers,
+    TJ *cval = reinterpret_cast<TJ *>(w.red + 2 * kBW);                        // double-buffered
+    int *crow = w.ired;
     if (t < n) w.perm[t] = int16_t(t);
-    __syncthreads();
-    for (int k = 0; k < n; ++k) {
-        // pivot: first row of largest |a_ik|, i >= k (thread t inspects row k + t)
-        double best = -1.0;
-        int bi = n;
+    int buf = 0;
+    for (int k0 = 0; k0 < n; k0 += kNB) {
+        const int kb = min(kNB, n - k0);
+        const int i = k0 + t;   // the panel row this thread owns
         {
-            const int i = k + t;
-            if (i < n) {
-                double a = fabs(double(w.J[size_t(i) * P + k]));
-                if (a != a) a = INFINITY;   // a NaN candidate fails the factorisation below
-                best = a;
-                bi = i;
+            unsigned long long best = 0;
+            TJ bv = TJ(0);
+            int bi = n;
+            if (i < n) pivot_candidate(J[size_t(i) * P + k0], i, best, bv, bi);
+            warp_argmax(best, bv, bi);
+            if (lane == 0) {
+                ckey[buf + wid] = best;
+                cval[buf + wid] = bv;
+                crow[buf + wid] = bi;
             }
         }
+        for (int c = 0; c < kb; ++c) {
+            const int k = k0 + c;
+            __syncthreads();   // offers for column k are written, the previous step's rows updated
+            unsigned long long best = ckey[buf];
+            TJ pv = cval[buf];
+            int p = crow[buf];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ob = __shfl_xor_sync(kFull, best, o);
-            const int oi = __shfl_xor_sync(kFull, bi, o);
-            if (ob > best || (ob == best && oi < bi)) {
-                best = ob;
-                bi = oi;
+            for (int u = 1; u < kBW; ++u) {
+                const unsigned long long ob = ckey[buf + u];
+                const int oi = crow[buf + u];
+                if (ob > best || (ob == best && oi < p)) {
+                    best = ob;
+                    pv = cval[buf + u];
+                    p = oi;
+                }
+            }
+            if (!key_is_finite_nonzero(abs_key(pv)) || p >= n) return false;
+            if (p != k) {
+                for (int j = t; j < n; j += kBT) {
+                    const TJ tmp = J[size_t(k) * P + j];
+                    J[size_t(k) * P + j] = J[size_t(p) * P + j];
+                    J[size_t(p) * P + j] = tmp;
+                }
+                if (t == 0) {
+                    const int16_t tp = w.perm[k];
+                    w.perm[k] = w.perm[p];
+                    w.perm[p] = tp;
+                }
+            }
+            __syncthreads();   // pivot row in place
+            buf = kBW - buf;
+            const TJ inv = TJ(1.0) / pv;
+            unsigned long long nb_best = 0;
+            TJ nb_v = TJ(0);
+            int nb_i = n;
+            if (i > k && i < n) {
+                TJ *ri = J + size_t(i) * P;
+                const TJ *rk = J + size_t(k) * P;
+                const TJ l = ri[k] * inv;
+                ri[k] = l;
+                for (int cc = k + 1; cc < k0 + kb; ++cc) ri[cc] = fma(-l, rk[cc], ri[cc]);
+                if (c + 1 < kb) pivot_candidate(ri[k + 1], i, nb_best, nb_v, nb_i);
+            }
+            if (c + 1 < kb) {
+                warp_argmax(nb_best, nb_v, nb_i);
+                if (lane == 0) {
+                    ckey[buf + wid] = nb_best;
+                    cval[buf + wid] = nb_v;
+                    crow[buf + wid] = nb_i;
+                }
             }
         }
-        if (lane == 0) {
-            w.red[wid] = best;
-            w.ired[wid] = bi;
+        const int r0 = k0 + kb;   // first row / column of the trailing matrix
+        if (r0 >= n) break;
+        __syncthreads();   // panel factored
+        // U12 = L11^-1 A12: one column per thread, forward substitution down the kb rows
+        {
+            const int j = r0 + t;
+            if (j < n) {
+                for (int r = 1; r < kb; ++r) {
+                    const TJ *Lr = J + size_t(k0 + r) * P + k0;
+                    TJ s0 = J[size_t(k0 + r) * P + j], s1 = TJ(0);
+                    int c = 0;
+                    for (; c + 1 < r; c += 2) {
+                        s0 = fma(-Lr[c], J[size_t(k0 + c) * P + j], s0);
+                        s1 = fma(-Lr[c + 1], J[size_t(k0 + c + 1) * P + j], s1);
+                    }
+                    if (c < r) s0 = fma(-Lr[c], J[size_t(k0 + c) * P + j], s0);
+                    J[size_t(k0 + r) * P + j] = s0 + s1;
+                }
+            }
         }
         __syncthreads();
-        best = w.red[0];
-        bi = w.ired[0];
+        // A22 -= L21 U12 in chunks of (16 TA) x 128
+        const int m = n - r0;
+        constexpr int kTA = TileRows<TJ>::value;
+        for (int rb = 0; rb < m; rb += 16 * kTA) {
+            for (int cb = 0; cb < m; cb += 32 * kTB) {
+                TJ acc[kTA][kTB];
 #pragma unroll
-        for (int u = 1; u < kBW; ++u) {
-            const double ob = w.red[u];
-            const int oi = w.ired[u];
-            if (ob > best || (ob == best && oi < bi)) {
-                best = ob;
-                bi = oi;
+                for (int a = 0; a < kTA; ++a)
+#pragma unroll
+                    for (int b = 0; b < kTB; ++b) acc[a][b] = TJ(0);
+                const int row0 = r0 + rb + wid, col0 = r0 + cb + lane;
+                for (int c = 0; c < kb; ++c) {
+                    TJ lv[kTA], uv[kTB];
+#pragma unroll
+                    for (int a = 0; a < kTA; ++a) {
+                        const int row = row0 + 16 * a;
+                        lv[a] = (row < n) ? J[size_t(row) * P + k0 + c] : TJ(0);
+                    }
+#pragma unroll
+                    for (int b = 0; b < kTB; ++b) {
+                        const int col = col0 + 32 * b;
+                        uv[b] = (col < n) ? J[size_t(k0 + c) * P + col] : TJ(0);
+                    }
+#pragma unroll
+                    for (int a = 0; a < kTA; ++a)
+#pragma unroll
+                        for (int b = 0; b < kTB; ++b) acc[a][b] = fma(lv[a], uv[b], acc[a][b]);
+                }
+#pragma unroll
+                for (int a = 0; a < kTA; ++a) {
+                    const int row = row0 + 16 * a;
+                    if (row < n) {
+#pragma unroll
+                        for (int b = 0; b < kTB; ++b) {
+                            const int col = col0 + 32 * b;
+                            if (col < n) J[size_t(row) * P + col] -= acc[a][b];
+                        }
+                    }
+                }
             }
         }
-        const int p = bi;
-        const double pv = (p < n) ? double(w.J[size_t(p) * P + k]) : 0.0;
-        __syncthreads();   // partials and the pivot are read before anything overwrites them
-        if (!(pv != 0.0) || !isfinite(pv)) return false;
-        if (p != k) {
-            for (int j = t; j < n; j += kBT) {
-                const TJ tmp = w.J[size_t(k) * P + j];
-                w.J[size_t(k) * P + j] = w.J[size_t(p) * P + j];
-                w.J[size_t(p) * P + j] = tmp;
-            }
-            if (t == 0) {
-                const int16_t tp = w.perm[k];
-                w.perm[k] = w.perm[p];
-                w.perm[p] = tp;
-            }
-            __syncthreads();
-        }
-        const TJ inv = TJ(1.0) / TJ(pv);
-        const TJ *rk = w.J + size_t(k) * P;
-        for (int r = k + 1 + wid; r < n; r += kBW) {
-            TJ *ri = w.J + size_t(r) * P;
-            const TJ l = ri[k] * inv;
-            for (int j = k + 1 + lane; j < n; j += 32) ri[j] = fma(-l, rk[j], ri[j]);
-            __syncwarp();   // every lane has read ri[k]
-            if (lane == 0) ri[k] = l;
-        }
-        __syncthreads();
+        __syncthreads();   // trailing matrix updated before the next panel reads it
     }
+    __syncthreads();
     return true;
 }
 
-// x = -(LU)^-1 r (r, x shared vectors of length n); the substitutions run on warp 0.
+// x = -(LU)^-1 r (r, x shared vectors of length n). Blocked substitutions: warp 0 solves
+// each 32 x 32 diagonal block with the unknowns in registers (shuffles), then every thread
+// updates one remaining row with that block's 32 unknowns.
 template <class TJ>
 __device__ void b_lu_solve_neg(const BWS<TJ> &w, int n, const double *r, double *x) {
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const int P = w.P;
     __syncthreads();   // r complete
     if (t < n) w.rhs[t] = TJ(-r[w.perm[t]]);
     __syncthreads();
-    if (t < 32) {
-        const int lane = t;
-        for (int k = 0; k < n - 1; ++k) {
-            const TJ bk = w.rhs[k];
-            for (int i = k + 1 + lane; i < n; i += 32) w.rhs[i] = fma(-w.J[size_t(i) * P + k], bk, w.rhs[i]);
-            __syncwarp();
+    const int nb = (n + 31) / 32;
+    // forward: unit lower
+    for (int b = 0; b < nb; ++b) {
+        const int r0 = b * 32, r1 = min(n, r0 + 32);
+        if (wid == 0) {
+            const int i = r0 + lane;
+            TJ xi = (i < r1) ? w.rhs[i] : TJ(0);
+            for (int c = r0; c < r1 - 1; ++c) {
+                const TJ xc = __shfl_sync(kFull, xi, c - r0);
+                if (i > c && i < r1) xi = fma(-w.J[size_t(i) * P + c], xc, xi);
+            }
+            if (i < r1) w.rhs[i] = xi;
         }
-        for (int k = n - 1; k >= 0; --k) {
-            const TJ xk = w.rhs[k] / w.J[size_t(k) * P + k];
-            __syncwarp();
-            for (int i = lane; i < k; i += 32) w.rhs[i] = fma(-w.J[size_t(i) * P + k], xk, w.rhs[i]);
-            if (lane == 0) w.rhs[k] = xk;
-            __syncwarp();
+        __syncthreads();
+        for (int i = r1 + t; i < n; i += kBT) {
+            const TJ *Li = w.J + size_t(i) * P;
+            TJ s = w.rhs[i];
+            for (int c = r0; c < r1; ++c) s = fma(-Li[c], w.rhs[c], s);
+            w.rhs[i] = s;
         }
+        __syncthreads();
     }
-    __syncthreads();
+    // backward: upper
+    for (int b = nb - 1; b >= 0; --b) {
+        const int r0 = b * 32, r1 = min(n, r0 + 32);
+        if (wid == 0) {
+            const int i = r0 + lane;
+            TJ xi = (i < r1) ? w.rhs[i] : TJ(0);
+            for (int c = r1 - 1; c >= r0; --c) {
+                const TJ own = (i == c) ? xi / w.J[size_t(c) * P + c] : xi;
+                const TJ xc = __shfl_sync(kFull, own, c - r0);
+                if (i == c) xi = xc;
+                else if (i < c) xi = fma(-w.J[size_t(i) * P + c], xc, xi);
+            }
+            if (i < r1) w.rhs[i] = xi;
+        }
+        __syncthreads();
+        for (int i = t; i < r0; i += kBT) {
+            const TJ *Ui = w.J + size_t(i) * P;
+            TJ s = w.rhs[i];
+            for (int c = r0; c < r1; ++c) s = fma(-Ui[c], w.rhs[c], s);
+            w.rhs[i] = s;
+        }
+        __syncthreads();
+    }
     if (t < n) x[t] = double(w.rhs[t]);
     __syncthreads();
 }
@@ -650,7 +790,7 @@ __device__ bool b_damped_newton(BCtx &cx, const BWS<TJ> &w, double *y, const dou
         if (counter >= o.max_newton) break;
         ++counter;
         b_eval_J(cx.M, w, c, cx.mx, cx.tau, o.energy, cx.mult);
-        if (!b_lu_factor(w, n)) break;
+        if (!b_lu(w, n)) break;
         b_lu_solve_neg(w, n, w.R, w.dy);
         if (!b_all_finite(w.dy, n)) break;
         bool done;
@@ -711,14 +851,15 @@ template <class TJ>
 __device__ void b_load_reactor(BCtx &cx, const BWS<TJ> &w, const Batch &bt, int64_t r) {
     const int t = threadIdx.x;
     const int K = cx.K;
-    cx.Yin = bt.Y_in + r * K;
+    const int64_t row = row_of(bt, r, K);
+    cx.Yin = bt.Y_in + row;
     cx.tau = bt.tau[r];
     cx.P = bt.P[r];
     cx.Tspec = bt.T0[r];
     cx.nfev = 0;
     b_inlet_enthalpy(cx, bt.T_in[r], w.red);
     if (t < cx.n) {
-        w.x[t] = (t < K) ? bt.Y0[r * K + t] : bt.T0[r];
+        w.x[t] = (t < K) ? bt.Y0[row + t] : bt.T0[r];
         w.c[t] = 0.0;
     }
     __syncthreads();
@@ -807,7 +948,7 @@ __device__ void b_solve_one(BCtx &cx, const BWS<TJ> &w, const Batch &bt, int64_t
     __syncthreads();
     b_residual_R(cx, w, out, w.c, out, w.F, w.R);
     const double fn = bmax(t < n ? fabs(w.F[t]) : 0.0, w.red);
-    if (t < K) bt.Y_out[r * K + t] = out[t];
+    if (t < K) bt.Y_out[row_of(bt, r, K) + t] = out[t];
     if (t == 0) {
         bt.T_out[r] = out[K];
         const bool fb = bt.fallback != 0;
@@ -835,9 +976,9 @@ __global__ void __launch_bounds__(kBT, 1) block_solve_kernel(DevMech M, Batch bt
     cx.n = n;
     const int64_t nwork = bt.list ? int64_t(*bt.list_len) : bt.B;
     while (true) {
-        if (threadIdx.x == 0) w.ired[kBW] = atomicAdd(queue, 1);
+        if (threadIdx.x == 0) w.ired[2 * kBW] = atomicAdd(queue, 1);
         __syncthreads();
-        const int p = w.ired[kBW];
+        const int p = w.ired[2 * kBW];
         __syncthreads();
         if (p >= nwork) break;
         const int64_t r = bt.list ? int64_t(bt.list[p]) : int64_t(p);
@@ -845,9 +986,13 @@ __global__ void __launch_bounds__(kBT, 1) block_solve_kernel(DevMech M, Batch bt
     }
 }
 
-__global__ void block_collect_unconverged(int64_t B, const int32_t *status, int32_t *list, int32_t *len) {
-    const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (r < B && status[r] != PSR_CONVERGED) list[atomicAdd(len, 1)] = int32_t(r);
+__global__ void block_collect_unconverged(int64_t B, const int32_t *in_list, const int32_t *in_len,
+                                          const int32_t *status, int32_t *list, int32_t *len) {
+    const int64_t n = in_list ? int64_t(*in_len) : B;
+    for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < n; p += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t r = in_list ? int64_t(in_list[p]) : p;
+        if (status[r] != PSR_CONVERGED) list[atomicAdd(len, 1)] = int32_t(r);
+    }
 }
 
 // residual or Jacobian at given states, one block per state (grid-stride over states)
@@ -900,7 +1045,7 @@ __global__ void __launch_bounds__(kBT, 1) block_adjoint_kernel(DevMech M, Batch 
         b_load_reactor(cx, w, bt, r);
         b_residual_R(cx, w, w.x, w.c, w.x, w.F, w.R);
         b_eval_J(M, w, w.c, cx.mx, cx.tau, energy, cx.mult);
-        const bool good = b_lu_factor(w, n);
+        const bool good = b_lu(w, n);
         if (t < n) {
             w.dy[t] = 0.0;
             w.db[t] = g[r * n + t];
@@ -944,7 +1089,7 @@ __global__ void __launch_bounds__(kBT, 1) block_lu_kernel(int64_t B, int n, cons
         for (int idx = t; idx < n * n; idx += kBT) w.J[size_t(idx / n) * w.P + idx % n] = TJ(A[b * n * n + idx]);
         if (t < n) w.R[t] = -rhs[b * n + t];
         __syncthreads();
-        const bool good = b_lu_factor(w, n);
+        const bool good = b_lu(w, n);
         if (good) b_lu_solve_neg(w, n, w.R, w.dy);
         if (t < n) x[b * n + t] = good ? w.dy[t] : 0.0;
         if (t == 0) ok[b] = good ? 1 : 0;
@@ -1034,7 +1179,8 @@ int block_solve(const Mech &m, const Batch &bt, const Opts &o, int precision, bo
         rc = launch_block<float>(m, b1, o, bps_req, st, scr);
         if (rc == PSR_OK) {
             cudaMemsetAsync(len, 0, sizeof(int32_t), st);
-            block_collect_unconverged<<<unsigned((B + 255) / 256), 256, 0, st>>>(bt.B, b1.status, list, len);
+            block_collect_unconverged<<<unsigned((B + 255) / 256), 256, 0, st>>>(bt.B, bt.list, bt.list_len,
+                                                                                 b1.status, list, len);
             e = cudaGetLastError();
             if (e != cudaSuccess) rc = cuda_error("block_collect_unconverged launch", e);
         }

@@ -32,6 +32,18 @@ __device__ __forceinline__ double wmin(double v) {
     return v;
 }
 
+// Pivot keys: the IEEE bits of |a| (sign cleared) order like |a| for every non-NaN value
+// and put NaN above infinity, so the pivot search runs on the integer pipe (GB300's FP64
+// pipe is the scarce one) and a NaN column is picked and then rejected.
+__device__ __forceinline__ uint32_t abs_key(float v) { return __float_as_uint(v) & 0x7fffffffu; }
+__device__ __forceinline__ unsigned long long abs_key(double v) {
+    return static_cast<unsigned long long>(__double_as_longlong(v)) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ bool key_is_finite_nonzero(uint32_t k) { return k != 0u && k < 0x7f800000u; }
+__device__ __forceinline__ bool key_is_finite_nonzero(unsigned long long k) {
+    return k != 0ull && k < 0x7ff0000000000000ull;
+}
+
 
 // ---------------------------------------------------------------- per-call parameters
 struct Batch {
@@ -44,7 +56,13 @@ struct Batch {
     const int32_t *list;       // optional work list of reactor indices (device), length *list_len
     const int32_t *list_len;
     int fallback;              // this launch re-solves the list in FP64 after a mixed launch
+    const int64_t *row_off;    // optional [B] start of reactor r's row in Y_in / Y0 / Y_out (else r K)
 };
+
+// Start of reactor r's mass-fraction row.
+__device__ __forceinline__ int64_t row_of(const Batch &bt, int64_t r, int K) {
+    return bt.row_off ? bt.row_off[r] : r * K;
+}
 
 struct Opts {
     double ftol, step_rtol, step_atol_y, step_atol_t, ts_rtol, ts_atol_y, dt0_over_tau, dt_shrink,
@@ -58,6 +76,21 @@ struct Mix {
     double N, cp, sum_yin_cp, sum_y_dcp;     // energy row pieces
     double h_in;                             // sum_k Y_k,in h_k(T_in), per reactor
 };
+
+// Per-species 1/W and per-entry efficiency - 1 in the Jacobian's precision (FP32 copies
+// avoid FP64-to-FP32 conversions, which run on the FP64 pipe, in the FP32 Jacobian).
+template <class TJ>
+__device__ __forceinline__ TJ inv_w(const DevMech &M, int j);
+template <>
+__device__ __forceinline__ double inv_w<double>(const DevMech &M, int j) { return __ldg(M.invW + j); }
+template <>
+__device__ __forceinline__ float inv_w<float>(const DevMech &M, int j) { return __ldg(M.invW_f + j); }
+template <class TJ>
+__device__ __forceinline__ TJ eff_v(const DevMech &M, int e);
+template <>
+__device__ __forceinline__ double eff_v<double>(const DevMech &M, int e) { return __ldg(M.eff_val + e); }
+template <>
+__device__ __forceinline__ float eff_v<float>(const DevMech &M, int e) { return __ldg(M.eff_val_f + e); }
 
 // ---------------------------------------------------------------- thermo (NASA-7)
 __device__ __forceinline__ void nasa7(const double *__restrict__ nasa, int k, double T, double lnT, double invT,

@@ -18,6 +18,7 @@ enum RxnType : int8_t { kElem = 0, kThirdBody = 1, kTroe = 2 };
 struct DevMech {
     int K, I, n_troe, n_eff;
     const double *W, *invW;      // [K] g/mol
+    const float *invW_f;         // [K] 1/W in FP32 (the FP32 Jacobian's transform)
     const double *nasa;          // [K][16]: T_mid, low a1..a7, high a1..a7, 0
     const double *lnA, *beta, *theta;   // [I] Eq. (6), E/R in K
     const int16_t *slots;        // [I][6] reactant slots 0..2, product slots 3..5, K = empty
@@ -27,6 +28,7 @@ struct DevMech {
     const int32_t *eff_ptr;      // [I+1] CSR of (efficiency - 1) for tb/troe rows
     const int16_t *eff_sp;       // [n_eff]
     const double *eff_val;       // [n_eff] eps - 1
+    const float *eff_val_f;      // [n_eff] the same in FP32
     const int32_t *troe_row;     // [I] row of troe params or -1
     const double *troe;          // [n_troe][8]: ln A0, beta0, E0/R, alpha, T3, T1, T2, 0
     const int32_t *sp_ptr;       // [K+1] CSR species -> reactions for wdot_k = sum nu_ki q_i

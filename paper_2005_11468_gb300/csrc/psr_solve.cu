@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <cfloat>
 #include <cmath>
 #include <cstdio>
@@ -172,7 +173,7 @@ __device__ __forceinline__ void soot_eval(const double *__restrict__ st, const d
 // ---------------------------------------------------------------- residual, Eqs. (2)-(9)
 // Evaluates F at state y; leaves C, hRT, gS, kf, kr (effective) of this state in shared
 // memory and the scalars/lane data in mx/sl for the Jacobian.
-template <class TJ>
+template <class TJ, bool SOOT>
 __device__ PSR_STAGE void eval_F(const DevMech &M, const WS<TJ> &w, const V2 &y, V2 &F, Mix &mx, SpecLane &sl,
                        const double *Yin_row, const double *Min, double tau, double P, double Tspec, int energy,
                        const double *__restrict__ mult) {
@@ -289,7 +290,7 @@ __device__ PSR_STAGE void eval_F(const DevMech &M, const WS<TJ> &w, const V2 &y,
     __syncwarp();
     // MOMIC sources (every lane evaluates them; the warp pays for one evaluation)
     double Ssoot[kNMom], sink = 0.0, zs[kNMom];
-    if (M.nsoot) {
+    if constexpr (SOOT) {
 #pragma unroll
         for (int r = 0; r < kNMom; ++r) zs[r] = comp_get(y, K + 1 + r);
         soot_eval(M.soot, zs, w.C[M.soot_P], T, Ssoot, sink);
@@ -312,7 +313,7 @@ __device__ PSR_STAGE void eval_F(const DevMech &M, const WS<TJ> &w, const V2 &y,
             }
             if (e < e_end) w0 += __ldg(M.sp_nu_d + e) * w.q[__ldg(M.sp_rxn + e)];
             double wd = w0 + w1;
-            if (M.nsoot) wd += (j == M.soot_H2 ? sink : 0.0) - (j == M.soot_P ? sink : 0.0);
+            if constexpr (SOOT) wd += (j == M.soot_H2 ? sink : 0.0) - (j == M.soot_P ? sink : 0.0);
             const double Yj = h ? y.b : y.a;
             const double f = Yj - Yin_row[j] - tau_rho * __ldg(M.W + j) * wd;
             s_hw += w.hRT[j] * wd;
@@ -339,7 +340,7 @@ __device__ PSR_STAGE void eval_F(const DevMech &M, const WS<TJ> &w, const V2 &y,
         else F.b = FT;
     }
     // moment balances F_r = (M_r - M_r,in - tau S_r) / (M_r + s_r)
-    if (M.nsoot) {
+    if constexpr (SOOT) {
         for (int h = 0; h < 2; ++h) {
             const int j = lane + 32 * h;
             if (j > K && j <= K + kNMom) {
@@ -365,12 +366,12 @@ __device__ PSR_STAGE void eval_F(const DevMech &M, const WS<TJ> &w, const V2 &y,
 // third-body part v_k for every column, sparse efficiency corrections), its Euler sums
 // s_k = sum_l Jc_kl [X_l] and T-derivatives wT_k, then the transform to (Y, T) through
 // rho(Y, T) and the energy row of Eq. (3). Entries are accumulated in TJ.
-template <class TJ>
+template <class TJ, bool SOOT>
 __device__ PSR_STAGE void eval_J(const DevMech &M, const WS<TJ> &w, const V2 &y, const V2 &c, const Mix &mx,
                                  const SpecLane &sl, const double *Yin_row, const double *Min, double tau,
                                  int energy, const double *__restrict__ mult) {
     const int lane = threadIdx.x & 31;
-    const int K = M.K, I = M.I, n = K + 1 + M.nsoot, P = w.P;
+    const int K = M.K, I = M.I, n = K + 1 + (SOOT ? kNMom : 0), P = w.P;
     // wdot (left in v[] by eval_F) moves to registers; v[] becomes the dense part
     double wd[2];
     for (int h = 0; h < 2; ++h) {
@@ -450,7 +451,7 @@ __device__ PSR_STAGE void eval_J(const DevMech &M, const WS<TJ> &w, const V2 &y,
             if (typ != kElem) {
                 atomicAdd(w.v + pl[r], double(pnu[r]) * dqdM);
                 for (int e = __ldg(M.eff_ptr + i); e < __ldg(M.eff_ptr + i + 1); ++e)
-                    atomicAdd(row + __ldg(M.eff_sp + e), pnu[r] * dqdM_t * TJ(__ldg(M.eff_val + e)));
+                    atomicAdd(row + __ldg(M.eff_sp + e), pnu[r] * dqdM_t * eff_v<TJ>(M, e));
             }
         }
         // per-reaction Euler sum and T-derivative replace q and kf (read by this lane only)
@@ -479,7 +480,10 @@ __device__ PSR_STAGE void eval_J(const DevMech &M, const WS<TJ> &w, const V2 &y,
     // energy row, Eq. (3): computed from the concentration Jacobian before the transform
     double eJ[2] = {0.0, 0.0};
     if (energy != PSR_FIXED_T) {
-        // Q = sum H_k wdot_k, Sh = sum H_k s_k, Hv = sum H_k v_k, dN/dT pieces
+        // Q = sum H_k wdot_k, Sh = sum H_k s_k, Hv = sum H_k v_k, dN/dT pieces; H/RT staged
+        // in the Jacobian's precision for the column sums
+        for (int k = lane; k < K; k += 32) w.rhs[k] = TJ(w.hRT[k]);
+        __syncwarp();
         double Q = 0.0, Sh = 0.0, Hv = 0.0, cw = 0.0, hwT = 0.0;
         for (int h = 0; h < 2; ++h) {
             int j = lane + 32 * h;
@@ -503,7 +507,7 @@ __device__ PSR_STAGE void eval_J(const DevMech &M, const WS<TJ> &w, const V2 &y,
             int j = lane + 32 * h;
             if (j < K) {
                 TJ colsum = TJ(0);
-                for (int k = 0; k < K; ++k) colsum += TJ(w.hRT[k]) * w.J[size_t(k) * P + j];
+                for (int k = 0; k < K; ++k) colsum += w.rhs[k] * w.J[size_t(k) * P + j];
                 const double cs = double(colsum) * RT + Hv;
                 const double invWj = __ldg(M.invW + j);
                 const double dN = tau * invWj * (cs + Wbar * (Q - Sh) / rho);
@@ -525,7 +529,7 @@ __device__ PSR_STAGE void eval_J(const DevMech &M, const WS<TJ> &w, const V2 &y,
             const TJ ak = TJ(tau * Wk), bk = TJ(tau * Wk * Wbar * (sk[h] - wd[h]) / rho), vkt = TJ(vk[h]);
             TJ *row = w.J + size_t(k) * P;
             for (int j = 0; j < K; ++j) {
-                const TJ invWj = TJ(__ldg(M.invW + j));
+                const TJ invWj = inv_w<TJ>(M, j);
                 row[j] = (bk - ak * (row[j] + vkt)) * invWj + ((j == k) ? TJ(1) : TJ(0));
             }
             row[K] = TJ(-(tau * Wk / rho) * (wT[h] + (wd[h] - sk[h]) * invT));
@@ -546,7 +550,7 @@ __device__ PSR_STAGE void eval_J(const DevMech &M, const WS<TJ> &w, const V2 &y,
         }
     }
     __syncwarp();
-    if (M.nsoot) {
+    if constexpr (SOOT) {
         // soot couplings: central differences of the source function in (zeta_0..5, CP, T),
         // lanes 0..16 each evaluating one perturbed input, chained through CP(Y, T)
         const int Psp = M.soot_P, Hsp = M.soot_H2;
@@ -643,30 +647,29 @@ __device__ PSR_STAGE bool lu_factor(const WS<TJ> &w, int n) {
     for (int j = lane; j < n; j += 32) w.perm[j] = int16_t(j);
     __syncwarp();
     for (int k = 0; k < n; ++k) {
-        // pivot: first row of largest |a_ik|, i >= k
-        double best = -1.0;
+        // pivot: first row of largest |a_ik|, i >= k (integer keys of |a|)
+        decltype(abs_key(TJ(0))) best = 0;
         int bi = n;
         for (int i = k + lane; i < n; i += 32) {
-            double a = fabs(double(w.J[size_t(i) * P + k]));
-            if (a > best || (a == best && i < bi) || a != a) {
-                if (a != a) a = INFINITY;  // a NaN pivot candidate fails the factorisation below
+            const auto a = abs_key(w.J[size_t(i) * P + k]);
+            if (a > best || (a == best && i < bi)) {
                 best = a;
                 bi = i;
             }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            double ob = __shfl_xor_sync(kFull, best, o);
-            int oi = __shfl_xor_sync(kFull, bi, o);
+            const auto ob = __shfl_xor_sync(kFull, best, o);
+            const int oi = __shfl_xor_sync(kFull, bi, o);
             if (ob > best || (ob == best && oi < bi)) {
                 best = ob;
                 bi = oi;
             }
         }
         const int p = bi;
-        const double pv = (p < n) ? double(w.J[size_t(p) * P + k]) : 0.0;
+        const TJ pv = (p < n) ? w.J[size_t(p) * P + k] : TJ(0);
         __syncwarp();   // every lane has read the pivot before the row swap overwrites it
-        if (!(pv != 0.0) || !isfinite(pv)) return false;
+        if (!key_is_finite_nonzero(abs_key(pv))) return false;
         if (p != k) {
             for (int j = lane; j < n; j += 32) {
                 TJ t = w.J[size_t(k) * P + j];
@@ -680,7 +683,7 @@ __device__ PSR_STAGE bool lu_factor(const WS<TJ> &w, int n) {
             }
         }
         __syncwarp();
-        const TJ inv = TJ(1.0) / TJ(pv);
+        const TJ inv = TJ(1.0) / pv;
         // multipliers and trailing update: lanes over rows
         for (int i = k + 1 + lane; i < n; i += 32) {
             TJ *ri = w.J + size_t(i) * P;
@@ -860,27 +863,28 @@ struct Ctx {
     int K, n;
 };
 
-template <class TJ>
+template <class TJ, bool SOOT>
 __device__ void residual_R(Ctx &cx, const WS<TJ> &w, const V2 &y, const V2 &c, const V2 &xref, V2 &F, V2 &R) {
     ++cx.nfev;
-    eval_F(cx.M, w, y, F, cx.mx, cx.sl, cx.r.Yin, cx.r.Min, cx.r.tau, cx.r.P, cx.r.Tspec, cx.o.energy, cx.mult);
+    eval_F<TJ, SOOT>(cx.M, w, y, F, cx.mx, cx.sl, cx.r.Yin, cx.r.Min, cx.r.tau, cx.r.P, cx.r.Tspec, cx.o.energy,
+                     cx.mult);
     R.a = F.a + c.a * (y.a - xref.a);
     R.b = F.b + c.b * (y.b - xref.b);
 }
 
 // Damped Newton on R(y) = F(y) + c (y - xref) from y (see the oracle's description).
-template <class TJ>
+template <class TJ, bool SOOT>
 __device__ bool damped_newton(Ctx &cx, const WS<TJ> &w, V2 &y, const V2 &xref, const V2 &c, int max_it,
                               bool steady, int &counter) {
     const int K = cx.K, n = cx.n;
     const Opts &o = cx.o;
     V2 F, R;
-    residual_R(cx, w, y, c, xref, F, R);
+    residual_R<TJ, SOOT>(cx, w, y, c, xref, F, R);
     double dn_prev = INFINITY;
     for (int it = 0; it < max_it; ++it) {
         if (counter >= o.max_newton) break;
         ++counter;
-        eval_J(cx.M, w, y, c, cx.mx, cx.sl, cx.r.Yin, cx.r.Min, cx.r.tau, o.energy, cx.mult);
+        eval_J<TJ, SOOT>(cx.M, w, y, c, cx.mx, cx.sl, cx.r.Yin, cx.r.Min, cx.r.tau, o.energy, cx.mult);
         if (!lu_factor(w, n)) break;
         V2 dy;
         lu_solve_neg(w, n, R, dy);
@@ -905,7 +909,7 @@ __device__ bool damped_newton(Ctx &cx, const WS<TJ> &w, V2 &y, const V2 &xref, c
             yt = axpy(y, lam, dy);
             if (in_bounds(yt, K, o)) {
                 V2 Ft;
-                residual_R(cx, w, yt, c, xref, Ft, Rt);
+                residual_R<TJ, SOOT>(cx, w, yt, c, xref, Ft, Rt);
                 if (all_finite(Rt)) {
                     V2 db;
                     lu_solve_neg(w, n, Rt, db);
@@ -966,14 +970,15 @@ __device__ void init_moments(Ctx &cx, const Batch &bt, int64_t r, V2 &x) {
     }
 }
 
-template <class TJ>
+template <class TJ, bool SOOT>
 __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) {
     const int lane = threadIdx.x & 31;
     const int K = cx.K;
     const Opts &o = cx.o;
     const double tau = bt.tau[r];
-    cx.r.Yin = bt.Y_in + r * K;
-    cx.r.Min = (cx.M.nsoot && bt.M_in) ? bt.M_in + r * kNMom : nullptr;
+    const int64_t row = row_of(bt, r, K);
+    cx.r.Yin = bt.Y_in + row;
+    cx.r.Min = (SOOT && bt.M_in) ? bt.M_in + r * kNMom : nullptr;
     cx.r.tau = tau;
     cx.r.P = bt.P[r];
     cx.r.Tspec = bt.T0[r];
@@ -993,12 +998,12 @@ __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) 
         cx.mx.h_in = wsum(s) * kRu * Tin;
     }
     V2 x;
-    x.a = (lane < K) ? bt.Y0[r * K + lane] : (lane == K ? bt.T0[r] : 0.0);
-    x.b = (lane + 32 < K) ? bt.Y0[r * K + lane + 32] : (lane + 32 == K ? bt.T0[r] : 0.0);
-    if (cx.M.nsoot) init_moments(cx, bt, r, x);
+    x.a = (lane < K) ? bt.Y0[row + lane] : (lane == K ? bt.T0[r] : 0.0);
+    x.b = (lane + 32 < K) ? bt.Y0[row + lane + 32] : (lane + 32 == K ? bt.T0[r] : 0.0);
+    if constexpr (SOOT) init_moments(cx, bt, r, x);
     const V2 zero{0.0, 0.0};
     V2 F, R;
-    residual_R(cx, w, x, zero, x, F, R);
+    residual_R<TJ, SOOT>(cx, w, x, zero, x, F, R);
     int status, counter = 0, ts = 0, rounds = 0;
     V2 out = x;
     if (!all_finite(F)) {
@@ -1007,7 +1012,7 @@ __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) 
         double dt = o.dt0_over_tau * tau;
         while (true) {
             V2 y = x;
-            bool conv = damped_newton(cx, w, y, x, zero, o.max_newton, true, counter);
+            bool conv = damped_newton<TJ, SOOT>(cx, w, y, x, zero, o.max_newton, true, counter);
             if (conv) {
                 status = PSR_CONVERGED;
                 out = y;
@@ -1035,7 +1040,7 @@ __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) 
                 c.b = (lane + 32 < K) ? s : (lane + 32 == K ? sT : (lane + 32 < cx.n ? s : 0.0));
                 const int used0 = counter;
                 V2 y = x;
-                bool ok = damped_newton(cx, w, y, x, c, o.ts_newton, false, counter);
+                bool ok = damped_newton<TJ, SOOT>(cx, w, y, x, c, o.ts_newton, false, counter);
                 const int used = counter - used0;
                 if (counter >= o.max_newton) {
                     status = PSR_MAX_ITER;
@@ -1063,12 +1068,12 @@ __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) 
         }
     }
     // report ||F||_inf at the output state
-    residual_R(cx, w, out, zero, out, F, R);
+    residual_R<TJ, SOOT>(cx, w, out, zero, out, F, R);
     const double fn = wmax(fmax(fabs(F.a), fabs(F.b)));
-    if (lane < K) bt.Y_out[r * K + lane] = out.a;
-    if (lane + 32 < K) bt.Y_out[r * K + lane + 32] = out.b;
+    if (lane < K) bt.Y_out[row + lane] = out.a;
+    if (lane + 32 < K) bt.Y_out[row + lane + 32] = out.b;
     const double Tout = comp_get(out, K);
-    if (cx.M.nsoot && bt.M_out) {
+    if (SOOT && bt.M_out) {
         for (int h = 0; h < 2; ++h) {
             const int j = lane + 32 * h;
             if (j > K && j <= K + kNMom)
@@ -1093,18 +1098,19 @@ __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) 
 #endif
 constexpr int kMaxSolveWarps = 4;   // the solver kernel's block holds at most 4 warps (128 threads)
 constexpr int kDefaultSolveWarps = 2;   // measured best at K = 53 for both forms (finer shared-memory packing)
-template <class TJ>
+template <class TJ, bool SOOT>
 __global__ void __launch_bounds__(128, PSR_MIN_BLOCKS) solve_kernel(DevMech M, Batch bt, Opts o, int *queue,
                                                                    size_t ws_per_warp) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WS<TJ> w = carve<TJ>(smem + warp * ws_per_warp, M.K, M.I, M.K + 1 + M.nsoot, M.n_troe, M.nsoot);
+    constexpr int ns = SOOT ? kNMom : 0;
+    WS<TJ> w = carve<TJ>(smem + warp * ws_per_warp, M.K, M.I, M.K + 1 + ns, M.n_troe, ns);
     Ctx cx;
     cx.M = M;
     cx.o = o;
     cx.mult = bt.rate_mult;
     cx.K = M.K;
-    cx.n = M.K + 1 + M.nsoot;
+    cx.n = M.K + 1 + ns;
     const int64_t nwork = bt.list ? int64_t(*bt.list_len) : bt.B;
     while (true) {
         int p = 0;
@@ -1112,33 +1118,39 @@ __global__ void __launch_bounds__(128, PSR_MIN_BLOCKS) solve_kernel(DevMech M, B
         p = __shfl_sync(kFull, p, 0);
         if (p >= nwork) break;
         const int64_t r = bt.list ? int64_t(bt.list[p]) : int64_t(p);
-        solve_one<TJ>(cx, w, bt, r);
+        solve_one<TJ, SOOT>(cx, w, bt, r);
     }
 }
 
-// Work list of the reactors a mixed-precision launch left unconverged.
-__global__ void collect_unconverged(int64_t B, const int32_t *status, int32_t *list, int32_t *len) {
-    const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (r < B && status[r] != PSR_CONVERGED) list[atomicAdd(len, 1)] = int32_t(r);
+// Work list of the reactors a mixed-precision launch left unconverged (among in_list
+// when given, else among all B).
+__global__ void collect_unconverged(int64_t B, const int32_t *in_list, const int32_t *in_len, const int32_t *status,
+                                    int32_t *list, int32_t *len) {
+    const int64_t n = in_list ? int64_t(*in_len) : B;
+    for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < n; p += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t r = in_list ? int64_t(in_list[p]) : p;
+        if (status[r] != PSR_CONVERGED) list[atomicAdd(len, 1)] = int32_t(r);
+    }
 }
 
 // residual / Jacobian at given states: one warp per state
-template <class TJ>
+template <class TJ, bool SOOT>
 __global__ void eval_kernel(DevMech M, Batch bt, int energy, int want_J, double *out, size_t ws_per_warp) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r = int64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
     if (r >= bt.B) return;
-    WS<TJ> w = carve<TJ>(smem + warp * ws_per_warp, M.K, M.I, M.K + 1 + M.nsoot, M.n_troe, M.nsoot);
+    constexpr int ns = SOOT ? kNMom : 0;
+    WS<TJ> w = carve<TJ>(smem + warp * ws_per_warp, M.K, M.I, M.K + 1 + ns, M.n_troe, ns);
     Ctx cx;
     cx.M = M;
     cx.mult = bt.rate_mult;
     cx.K = M.K;
-    cx.n = M.K + 1 + M.nsoot;
+    cx.n = M.K + 1 + ns;
     cx.o.energy = energy;
     const int K = M.K, n = cx.n;
     cx.r.Yin = bt.Y_in + r * K;
-    cx.r.Min = M.nsoot ? bt.M_in + r * kNMom : nullptr;
+    cx.r.Min = SOOT ? bt.M_in + r * kNMom : nullptr;
     cx.r.tau = bt.tau[r];
     cx.r.P = bt.P[r];
     cx.r.Tspec = bt.T0[r];
@@ -1158,16 +1170,16 @@ __global__ void eval_kernel(DevMech M, Batch bt, int energy, int want_J, double 
     V2 y;
     y.a = (lane < K) ? bt.Y0[r * K + lane] : (lane == K ? bt.T0[r] : 0.0);
     y.b = (lane + 32 < K) ? bt.Y0[r * K + lane + 32] : (lane + 32 == K ? bt.T0[r] : 0.0);
-    if (M.nsoot) init_moments(cx, bt, r, y);       // bt.M0 holds the state's moments
+    if constexpr (SOOT) init_moments(cx, bt, r, y);       // bt.M0 holds the state's moments
     const V2 zero{0.0, 0.0};
     V2 F, R;
-    residual_R(cx, w, y, zero, y, F, R);
+    residual_R<TJ, SOOT>(cx, w, y, zero, y, F, R);
     if (!want_J) {
         if (lane < n) out[r * n + lane] = F.a;
         if (lane + 32 < n) out[r * n + lane + 32] = F.b;
         return;
     }
-    eval_J(M, w, y, zero, cx.mx, cx.sl, cx.r.Yin, cx.r.Min, cx.r.tau, energy, cx.mult);
+    eval_J<TJ, SOOT>(M, w, y, zero, cx.mx, cx.sl, cx.r.Yin, cx.r.Min, cx.r.tau, energy, cx.mult);
     for (int idx = lane; idx < n * n; idx += 32)
         out[r * n * n + idx] = double(w.J[size_t(idx / n) * w.P + idx % n]);
 }
@@ -1211,16 +1223,16 @@ __global__ void adjoint_kernel(DevMech M, Batch bt, int energy, const double *g,
     y.b = (lane + 32 < K) ? bt.Y0[r * K + lane + 32] : (lane + 32 == K ? bt.T0[r] : 0.0);
     const V2 zero{0.0, 0.0};
     V2 F, R;
-    residual_R(cx, w, y, zero, y, F, R);
+    residual_R<double, false>(cx, w, y, zero, y, F, R);
     cx.r.Min = nullptr;
-    eval_J(M, w, y, zero, cx.mx, cx.sl, cx.r.Yin, nullptr, cx.r.tau, energy, cx.mult);
+    eval_J<double, false>(M, w, y, zero, cx.mx, cx.sl, cx.r.Yin, nullptr, cx.r.tau, energy, cx.mult);
     const bool good = lu_factor(w, n);
     V2 gv, lam{0.0, 0.0};
     gv.a = (lane < n) ? g[r * n + lane] : 0.0;
     gv.b = (lane + 32 < n) ? g[r * n + lane + 32] : 0.0;
     if (good) lu_solve_T(w, n, gv, lam);
     // the Jacobian pass replaced q_i: evaluate the residual once more to restore it
-    residual_R(cx, w, y, zero, y, F, R);
+    residual_R<double, false>(cx, w, y, zero, y, F, R);
     if (lam_out) {
         if (lane < n) lam_out[r * n + lane] = lam.a;
         if (lane + 32 < n) lam_out[r * n + lane + 32] = lam.b;
@@ -1315,9 +1327,9 @@ int check_opts(const psr_options *po) {
     return PSR_OK;
 }
 
-template <class TJ>
-int launch_solve_q(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int bps_req, cudaStream_t st,
-                   int *queue) {
+template <class TJ, bool SOOT>
+int launch_solve_qs(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int bps_req, cudaStream_t st,
+                    int *queue) {
     const size_t wsb = ws_bytes<TJ>(m.K, m.I, m.K + 1 + m.dev.nsoot, m.n_troe, m.dev.nsoot);
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1329,10 +1341,11 @@ int launch_solve_q(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, i
     const size_t smem = size_t(wpb) * wsb;
     if (smem > size_t(max_smem))
         return set_error(PSR_E_UNSUPPORTED, "mechanism too large for one warp's shared memory");
-    cudaError_t e = cudaFuncSetAttribute(solve_kernel<TJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaError_t e = cudaFuncSetAttribute(solve_kernel<TJ, SOOT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(smem));
     if (e != cudaSuccess) return cuda_error("cudaFuncSetAttribute", e);
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel<TJ>, wpb * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel<TJ, SOOT>, wpb * 32, smem);
     if (e != cudaSuccess) return cuda_error("occupancy", e);
     if (per_sm < 1) return set_error(PSR_E_UNSUPPORTED, "solver kernel does not fit on an SM");
     if (bps_req > 0 && bps_req < per_sm) per_sm = bps_req;
@@ -1341,10 +1354,19 @@ int launch_solve_q(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, i
     if (grid < 1) grid = 1;
     e = cudaMemsetAsync(queue, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_error("cudaMemsetAsync(work queue)", e);
-    solve_kernel<TJ><<<unsigned(grid), wpb * 32, smem, st>>>(m.dev, bt, o, queue, wsb);
+    solve_kernel<TJ, SOOT><<<unsigned(grid), wpb * 32, smem, st>>>(m.dev, bt, o, queue, wsb);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error("solve_kernel launch", e);
     return PSR_OK;
+}
+
+// The gas-only and the gas + soot solver are separate instantiations (the soot code
+// would otherwise cost the gas kernel registers).
+template <class TJ>
+int launch_solve_q(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int bps_req, cudaStream_t st,
+                   int *queue) {
+    if (m.dev.nsoot) return launch_solve_qs<TJ, true>(m, bt, o, wpb_req, bps_req, st, queue);
+    return launch_solve_qs<TJ, false>(m, bt, o, wpb_req, bps_req, st, queue);
 }
 
 template <class TJ>
@@ -1375,7 +1397,8 @@ int launch_mixed(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int
     int rc = launch_solve_q<float>(m, b1, o, wpb_req, bps_req, st, q0);
     if (rc == PSR_OK) {
         cudaMemsetAsync(len, 0, sizeof(int32_t), st);
-        collect_unconverged<<<unsigned((B + 255) / 256), 256, 0, st>>>(bt.B, b1.status, list, len);
+        collect_unconverged<<<unsigned((B + 255) / 256), 256, 0, st>>>(bt.B, bt.list, bt.list_len, b1.status, list,
+                                                                       len);
         e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_error("collect_unconverged launch", e);
     }
@@ -1390,18 +1413,25 @@ int launch_mixed(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int
     return rc;
 }
 
-template <class TJ>
-int launch_eval(const Mech &m, const Batch &bt, int energy, int want_J, double *out, cudaStream_t st) {
+template <class TJ, bool SOOT>
+int launch_eval_s(const Mech &m, const Batch &bt, int energy, int want_J, double *out, cudaStream_t st) {
     const size_t wsb = ws_bytes<TJ>(m.K, m.I, m.K + 1 + m.dev.nsoot, m.n_troe, m.dev.nsoot);
     const int wpb = 2;
     const size_t smem = wpb * wsb;
-    cudaError_t e = cudaFuncSetAttribute(eval_kernel<TJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaError_t e =
+        cudaFuncSetAttribute(eval_kernel<TJ, SOOT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return cuda_error("cudaFuncSetAttribute", e);
     const int64_t grid = (bt.B + wpb - 1) / wpb;
-    eval_kernel<TJ><<<unsigned(grid), wpb * 32, smem, st>>>(m.dev, bt, energy, want_J, out, wsb);
+    eval_kernel<TJ, SOOT><<<unsigned(grid), wpb * 32, smem, st>>>(m.dev, bt, energy, want_J, out, wsb);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error("eval_kernel launch", e);
     return PSR_OK;
+}
+
+template <class TJ>
+int launch_eval(const Mech &m, const Batch &bt, int energy, int want_J, double *out, cudaStream_t st) {
+    if (m.dev.nsoot) return launch_eval_s<TJ, true>(m, bt, energy, want_J, out, st);
+    return launch_eval_s<TJ, false>(m, bt, energy, want_J, out, st);
 }
 
 // ---------------------------------------------------------------- allocation-free variant
@@ -1456,10 +1486,10 @@ int launch_solve_noalloc(const Mech &m, const Batch &bt, const Opts &o, int wpb_
     const size_t smem = size_t(wpb) * wsb;
     if (smem > size_t(max_smem))
         return set_error(PSR_E_UNSUPPORTED, "mechanism too large for one warp's shared memory");
-    cudaError_t e = cudaFuncSetAttribute(solve_kernel<TJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaError_t e = cudaFuncSetAttribute(solve_kernel<TJ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return cuda_error("cudaFuncSetAttribute", e);
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel<TJ>, wpb * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel<TJ, false>, wpb * 32, smem);
     if (e != cudaSuccess) return cuda_error("occupancy", e);
     if (per_sm < 1) return set_error(PSR_E_UNSUPPORTED, "solver kernel does not fit on an SM");
     if (bps_req > 0 && bps_req < per_sm) per_sm = bps_req;
@@ -1468,7 +1498,7 @@ int launch_solve_noalloc(const Mech &m, const Batch &bt, const Opts &o, int wpb_
     if (grid < 1) grid = 1;
     e = cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return cuda_error("cudaMemsetAsync(work queue)", e);
-    solve_kernel<TJ><<<unsigned(grid), wpb * 32, smem, st>>>(m.dev, bt, o, queue, wsb);
+    solve_kernel<TJ, false><<<unsigned(grid), wpb * 32, smem, st>>>(m.dev, bt, o, queue, wsb);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error("solve_kernel launch", e);
     return PSR_OK;
@@ -1487,6 +1517,48 @@ int check_mech(const psr_mech *m) {
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != m->m.device) return set_error(PSR_E_ARG, "mechanism was loaded on another CUDA device");
+    return PSR_OK;
+}
+
+// ---------------------------------------------------------------- several mechanisms in one call
+constexpr int kMaxMechs = 8;
+
+// Reactor r goes to the work list of its mechanism; an out-of-range id is reported.
+__global__ void bucket_by_mechanism(int64_t B, const int32_t *mech_id, int n_mech, int32_t *counts, int32_t *lists,
+                                    int32_t *status) {
+    for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < B; r += int64_t(gridDim.x) * blockDim.x) {
+        const int c = mech_id[r];
+        if (c < 0 || c >= n_mech) {
+            status[r] = PSR_BAD_INPUT;
+            continue;
+        }
+        lists[int64_t(c) * B + atomicAdd(counts + c, 1)] = int32_t(r);
+    }
+}
+
+// Per device: one stream per mechanism class and the fork/join events, created on first
+// use and kept until exit. The mutex serialises the (short) enqueue of concurrent callers.
+struct ClassStreams {
+    bool ready = false;
+    cudaStream_t s[kMaxMechs];
+    cudaEvent_t fork, join[kMaxMechs];
+};
+ClassStreams g_class[kMaxDevices];
+std::mutex g_class_mu;
+
+int class_streams(int dev, ClassStreams **out) {
+    if (dev < 0 || dev >= kMaxDevices) return set_error(PSR_E_UNSUPPORTED, "device index too large");
+    ClassStreams &c = g_class[dev];
+    if (!c.ready) {
+        cudaError_t e = cudaEventCreateWithFlags(&c.fork, cudaEventDisableTiming);
+        for (int i = 0; i < kMaxMechs && e == cudaSuccess; ++i) {
+            e = cudaStreamCreateWithFlags(&c.s[i], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.join[i], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_error("class streams", e);
+        c.ready = true;
+    }
+    *out = &c;
     return PSR_OK;
 }
 
@@ -1749,6 +1821,78 @@ int psr_batch_lu_solve(int64_t B, int32_t n, const double *A, const double *r, d
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error("lu_kernel launch", e);
     return PSR_OK;
+}
+
+int psr_batch_solve_multi(const psr_mech *const *mechs, int32_t n_mech, int64_t B, const int32_t *mech_id,
+                          const int64_t *row_off, const double *Y_in, const double *T_in, const double *tau,
+                          const double *P, const double *Y0, const double *T0, double *Y_out, double *T_out,
+                          int32_t *iters, int32_t *ts_steps, int32_t *status, double *fnorm, int32_t *nfev,
+                          const psr_options *opt, void *cuda_stream) {
+    if (!mechs || n_mech < 1 || n_mech > kMaxMechs) return set_error(PSR_E_ARG, "n_mech must be 1..8");
+    for (int c = 0; c < n_mech; ++c) {
+        const int rc = check_mech(mechs[c]);
+        if (rc) return rc;
+        if (mechs[c]->m.has_soot) return set_error(PSR_E_ARG, "psr_batch_solve_multi: gas mechanisms only");
+    }
+    if (B < 0) return set_error(PSR_E_ARG, "B < 0");
+    if (B == 0) return PSR_OK;
+    if (B > (int64_t(1) << 31) - 64) return set_error(PSR_E_ARG, "B too large");
+    if (!mech_id || !row_off || !Y_in || !T_in || !tau || !P || !Y0 || !T0 || !Y_out || !T_out)
+        return set_error(PSR_E_ARG, "psr_batch_solve_multi: required pointer is NULL");
+    int rc = check_opts(opt);
+    if (rc) return rc;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    ClassStreams *cs = nullptr;
+    if ((rc = class_streams(dev, &cs))) return rc;
+    const Opts o = to_opts(opt);
+    psr_options d;
+    psr_options_default(&d);
+    const psr_options &po = opt ? *opt : d;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // scratch: per-class counts and lists, and a status array when the caller passed none
+    const size_t nb = size_t(B);
+    int32_t *scr = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scr),
+                                    sizeof(int32_t) * (kMaxMechs + size_t(n_mech) * nb + (status ? 0 : nb)), st);
+    if (e != cudaSuccess) return set_error(PSR_E_OOM, "scratch allocation failed");
+    int32_t *counts = scr, *lists = scr + kMaxMechs;
+    int32_t *stat = status ? status : lists + size_t(n_mech) * nb;
+    cudaMemsetAsync(counts, 0, sizeof(int32_t) * kMaxMechs, st);
+    bucket_by_mechanism<<<unsigned(std::min<int64_t>((B + 255) / 256, 4096)), 256, 0, st>>>(B, mech_id, n_mech,
+                                                                                           counts, lists, stat);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        cudaFreeAsync(scr, st);
+        return cuda_error("bucket_by_mechanism launch", e);
+    }
+    // classes in order of decreasing size of the system, each on its own stream
+    int order[kMaxMechs];
+    for (int c = 0; c < n_mech; ++c) order[c] = c;
+    std::sort(order, order + n_mech, [&](int a, int b) { return mechs[a]->m.K > mechs[b]->m.K; });
+    std::lock_guard<std::mutex> lock(g_class_mu);
+    cudaEventRecord(cs->fork, st);
+    rc = PSR_OK;
+    for (int k = 0; k < n_mech && rc == PSR_OK; ++k) {
+        const int c = order[k];
+        cudaStream_t sc = cs->s[k];
+        cudaStreamWaitEvent(sc, cs->fork, 0);
+        Batch bt{B, Y_in, T_in, tau, P, Y0, T0, nullptr, Y_out, T_out, fnorm, iters, ts_steps, stat, nfev};
+        bt.list = lists + size_t(c) * nb;
+        bt.list_len = counts + c;
+        bt.row_off = row_off;
+        const Mech &mm = mechs[c]->m;
+        if (!warp_path(mechs[c]))
+            rc = block_solve(mm, bt, o, po.precision, po.mixed_fallback != 0, po.blocks_per_sm, sc);
+        else if (po.precision == PSR_MIXED)
+            rc = launch_mixed(mm, bt, o, po.warps_per_block, po.blocks_per_sm, po.mixed_fallback != 0, sc);
+        else
+            rc = launch_solve<double>(mm, bt, o, po.warps_per_block, po.blocks_per_sm, sc);
+        cudaEventRecord(cs->join[k], sc);
+        cudaStreamWaitEvent(st, cs->join[k], 0);
+    }
+    cudaFreeAsync(scr, st);
+    return rc;
 }
 
 }  // extern "C"

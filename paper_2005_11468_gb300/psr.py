@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libpsr.so")
 
 PSR_OK = 0
 PSR_CONVERGED, PSR_MAX_ITER, PSR_NONFINITE, PSR_TS_EXHAUSTED, PSR_REFINE_FALLBACK = 0, 1, 2, 4, 5
+PSR_BAD_INPUT = 7
 CONVERGED_STATES = (PSR_CONVERGED, PSR_REFINE_FALLBACK)
 PSR_FP64, PSR_MIXED = 0, 1
 PSR_ADIABATIC, PSR_FIXED_T = 0, 1
@@ -79,6 +80,8 @@ def lib():
         L.psr_batch_solve_soot.argtypes = [vp, i64] + [dp] * 9 + [dp] * 3 + [dp] * 5 + [ctypes.POINTER(COptions), vp]
         L.psr_eval_residual_soot.argtypes = [vp, i64] + [dp] * 9 + [dp, i32, vp]
         L.psr_eval_jacobian_soot.argtypes = [vp, i64] + [dp] * 9 + [dp, i32, i32, vp]
+        L.psr_batch_solve_multi.argtypes = [ctypes.POINTER(vp), i32, i64, dp, dp] + [dp] * 8 + [dp] * 5 + \
+            [ctypes.POINTER(COptions), vp]
         _lib = L
     return _lib
 
@@ -357,3 +360,30 @@ def eval_jacobian_soot(mech: Mechanism, Y_in, T_in, tau, P, M_in, Y, T, M, rate_
         _ptr(M_in, f64, (B, 6)), _ptr(Y, f64, (B, K)), _ptr(T, f64, (B,)), _ptr(M, f64, (B, 6)),
         _ptr(rate_mult, f64, (mech.I,)), J.data_ptr(), energy, precision, _stream()))
     return J
+
+
+def batch_solve_multi(mechs, mech_id, row_off, Y_in, T_in, tau, P, Y0, T0, opts: Options = None, out=None):
+    """psr_batch_solve_multi: B reactors of several mechanisms in one call. mech_id (int32
+    [B]) picks mechs[mech_id[r]]; row_off (int64 [B]) locates reactor r's row in the packed
+    float64 arrays Y_in, Y0 (and the returned Y). Returns dict Y (packed), T, iters,
+    ts_steps, status, fnorm, nfev."""
+    import torch
+    f64, i32, i64 = torch.float64, torch.int32, torch.int64
+    B = mech_id.shape[0]
+    L = Y_in.shape[0]
+    dev = Y_in.device
+    if out is None:
+        out = dict(Y=torch.empty(L, dtype=f64, device=dev), T=torch.empty(B, dtype=f64, device=dev),
+                   iters=torch.empty(B, dtype=i32, device=dev), ts_steps=torch.empty(B, dtype=i32, device=dev),
+                   status=torch.empty(B, dtype=i32, device=dev), fnorm=torch.empty(B, dtype=f64, device=dev),
+                   nfev=torch.empty(B, dtype=i32, device=dev))
+    handles = (ctypes.c_void_p * len(mechs))(*[m.handle for m in mechs])
+    o = (opts or Options()).to_c()
+    _check(lib().psr_batch_solve_multi(
+        handles, len(mechs), B, _ptr(mech_id, i32, (B,), "mech_id"), _ptr(row_off, i64, (B,), "row_off"),
+        _ptr(Y_in, f64, (L,), "Y_in"), _ptr(T_in, f64, (B,), "T_in"), _ptr(tau, f64, (B,), "tau"),
+        _ptr(P, f64, (B,), "P"), _ptr(Y0, f64, (L,), "Y0"), _ptr(T0, f64, (B,), "T0"),
+        _ptr(out["Y"], f64, (L,)), _ptr(out["T"], f64, (B,)), _ptr(out["iters"], i32, (B,)),
+        _ptr(out["ts_steps"], i32, (B,)), _ptr(out["status"], i32, (B,)), _ptr(out["fnorm"], f64, (B,)),
+        _ptr(out["nfev"], i32, (B,)), ctypes.byref(o), _stream()))
+    return out

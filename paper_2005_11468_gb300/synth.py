@@ -91,6 +91,14 @@ class MechanismSpec:
     def I(self):
         return len(self.reactions)
 
+    @property
+    def n_tb(self):
+        return sum(r.kind == "tb" for r in self.reactions)
+
+    @property
+    def n_troe(self):
+        return sum(r.kind == "troe" for r in self.reactions)
+
 
 def _name(c):
     s = ""
@@ -427,3 +435,34 @@ def mixed_assignment(B=None, seed=None):
     counts[0] = B - counts[1] - counts[2]
     ids = np.concatenate([np.full(c, j, dtype=np.int32) for j, c in enumerate(counts)])
     return ids[rng.permutation(B)]
+
+
+def mixed_batch(specs, B=None, seed=None):
+    """The uneven batch: mech ids from mixed_assignment, and for each mechanism class a
+    batch of its own (make_batch, seed base + 10 tag + 2 + class) whose rows go, in order,
+    to that class's reactors. Returns a dict with mech_id [B], row_off [B] (offsets into the
+    packed rows), packed Y_in / Y0, per-reactor T_in, tau, P, T0, and per class the
+    reactor indices and its Batch."""
+    ids = mixed_assignment(B, seed)
+    B = ids.shape[0]
+    K = np.array([s.K for s in specs])
+    row_len = K[ids]
+    row_off = np.zeros(B, dtype=np.int64)
+    row_off[1:] = np.cumsum(row_len)[:-1]
+    L = int(row_len.sum())
+    out = dict(mech_id=ids, row_off=row_off, Y_in=np.zeros(L), Y0=np.zeros(L), T_in=np.zeros(B),
+               tau=np.zeros(B), P=np.zeros(B), T0=np.zeros(B), members=[], batches=[])
+    base = MECH_SEED_BASE + 10 * MIXED_WORKLOAD["tag"] + 2
+    for c, spec in enumerate(specs):
+        members = np.flatnonzero(ids == c)
+        bc = make_batch(spec, max(len(members), 1), seed=base + c)
+        bc = bc.subset(range(len(members)))
+        for j, r in enumerate(members):
+            o = row_off[r]
+            out["Y_in"][o:o + spec.K] = bc.Y_in[j]
+            out["Y0"][o:o + spec.K] = bc.Y0[j]
+        for k in ("T_in", "tau", "P", "T0"):
+            out[k][members] = getattr(bc, k)
+        out["members"].append(members)
+        out["batches"].append(bc)
+    return out
