@@ -204,6 +204,33 @@ int psr_batch_solve_multi(const psr_mech *const *mechs, int32_t n_mech, int64_t 
                           int32_t *iters, int32_t *ts_steps, int32_t *status, double *fnorm,
                           int32_t *nfev, const psr_options *opt, void *cuda_stream);
 
+/* Autotuner for the launch shape (the paper has no counterpart; a service of the
+ * library): solves the caller's sample batch (device arrays as psr_batch_solve, B >= 1,
+ * ideally a few thousand reactors like the production batches) once per candidate shape
+ * and writes the one with the most converged solves per second into opt->warps_per_block
+ * and opt->blocks_per_sm; every other field of *opt is used as given. Candidates on the
+ * warp path: 1..4 warps per block, and 2-warp blocks capped at 2..4 blocks per SM; the
+ * block path (K + 1 > 64) has a single shape (warps_per_block = 0, blocks_per_sm = 0).
+ * Synchronises cuda_stream; allocates and frees output scratch on it. Results of the
+ * solver do not depend on the shape (one warp per reactor either way).
+ * Errors: PSR_E_ARG (NULL, soot mechanism, B outside 1..2^24), PSR_E_CUDA, PSR_E_OOM. */
+int psr_autotune(const psr_mech *m, int64_t B,
+                 const double *Y_in, const double *T_in, const double *tau, const double *P,
+                 const double *Y0, const double *T0, psr_options *opt, void *cuda_stream);
+
+/* Rates at given states, the unit the paper times on its GPU (Secs. 4 and 6: forward
+ * rate constants, Eq. (6); equilibrium constants and reverse rates, Eqs. (7)-(9); rates of
+ * progress, Eq. (5); net production, Eq. (4)). Y [B][K], T [B] (K), P [B] (dyn/cm^2):
+ * device arrays; rate_mult [I] or NULL as in psr_batch_solve. Outputs (device, each may
+ * be NULL): kf_out, kr_out, q_out [B][I] in the mechanism file's reaction order, wdot_out
+ * [B][K] (mol/cm^3/s). kf is the effective forward coefficient (times the Troe factor
+ * P_r/(1+P_r) F for falloff reactions; the third-body [M] multiplies q, not kf); kr =
+ * kf / K_c; q includes [M] and rate_mult. Gas mechanisms only.
+ * Errors: PSR_E_ARG, PSR_E_UNSUPPORTED, PSR_E_CUDA. */
+int psr_eval_rates(const psr_mech *m, int64_t B, const double *Y, const double *T, const double *P,
+                   const double *rate_mult, double *kf_out, double *kr_out, double *q_out,
+                   double *wdot_out, void *cuda_stream);
+
 /* Same as psr_batch_solve with every array in HOST memory: the call copies the inputs
  * to the device, solves, copies the outputs back and synchronises the stream before
  * returning. Device buffers are allocated and freed inside the call. */

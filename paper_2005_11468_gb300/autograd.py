@@ -34,7 +34,8 @@ class PSRSolve(torch.autograd.Function):
             g[:, K] = gT
         grad, _, ok = psr.batch_adjoint(ctx.mech, Y_in, T_in, tau, P, Y, T, g.contiguous(),
                                         rate_mult=mult, energy=ctx.energy)
-        valid = (status == psr.PSR_CONVERGED) & (ok == 1)
+        conv = (status == psr.PSR_CONVERGED) | (status == psr.PSR_REFINE_FALLBACK)
+        valid = conv & (ok == 1)
         grad = torch.where(valid[:, None], grad, torch.zeros_like(grad))
         return grad.sum(0), None, None, None, None, None, None, None, None
 

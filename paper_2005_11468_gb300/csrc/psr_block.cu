@@ -343,8 +343,8 @@ __device__ void b_eval_J(const DevMech &M, const BWS<TJ> &w, const double *c, co
             pl[u] = __ldg(pp + u);
             pnu[u] = TJ(__ldg(pn + u));
             const int fm = __ldg(pfm + u), rm = __ldg(prm + u);
-            const double dfl = ((fm & 1) ? d0 : 0.0) + ((fm & 2) ? d1 : 0.0) + ((fm & 4) ? d2 : 0.0);
-            const double drl = ((rm & 1) ? d3 : 0.0) + ((rm & 2) ? d4 : 0.0) + ((rm & 4) ? d5 : 0.0);
+            const double dfl = slot_deriv(fm, d0, d1, d2);
+            const double drl = slot_deriv(rm, d3, d4, d5);
             val[u] = TJ(Af * dfl - Ar * drl);
         }
         const TJ dqdM_t = TJ(dqdM);
@@ -998,7 +998,7 @@ __global__ void block_collect_unconverged(int64_t B, const int32_t *in_list, con
 // residual or Jacobian at given states, one block per state (grid-stride over states)
 template <class TJ>
 __global__ void __launch_bounds__(kBT, 1) block_eval_kernel(DevMech M, Batch bt, int energy, int want_J,
-                                                            double *out, TJ *Jglob) {
+                                                            double *out, RatesOut ro, TJ *Jglob) {
     extern __shared__ __align__(16) char smem[];
     const int K = M.K, n = K + 1;
     const size_t slot = size_t(n) * pitch_of(n);
@@ -1013,6 +1013,17 @@ __global__ void __launch_bounds__(kBT, 1) block_eval_kernel(DevMech M, Batch bt,
     for (int64_t r = blockIdx.x; r < bt.B; r += gridDim.x) {
         b_load_reactor(cx, w, bt, r);
         b_residual_R(cx, w, w.x, w.c, w.x, w.F, w.R);
+        if (want_J == 2) {   // rates of the residual just evaluated: effective kf, kr, q_i, wdot_k
+            for (int i = t; i < M.I; i += kBT) {
+                const int64_t o = r * M.I + __ldg(M.orig + i);
+                if (ro.kf) ro.kf[o] = w.kf[i];
+                if (ro.kr) ro.kr[o] = w.kr[i];
+                if (ro.q) ro.q[o] = w.q[i];
+            }
+            if (ro.wdot && t < K) ro.wdot[r * K + t] = w.v[t];
+            __syncthreads();
+            continue;
+        }
         if (!want_J) {
             if (t < n) out[r * n + t] = w.F[t];
             continue;
@@ -1197,7 +1208,8 @@ int block_solve(const Mech &m, const Batch &bt, const Opts &o, int precision, bo
 }
 
 template <class TJ>
-static int block_eval_t(const Mech &m, const Batch &bt, int energy, int want_J, double *out, cudaStream_t st) {
+static int block_eval_t(const Mech &m, const Batch &bt, int energy, int want_J, double *out, cudaStream_t st,
+                        RatesOut ro) {
     const int K = m.K, n = K + 1;
     Launch L;
     int rc = plan<TJ>(block_eval_kernel<TJ>, K, m.I, m.n_troe, n, bt.B, 0, L);
@@ -1208,16 +1220,17 @@ static int block_eval_t(const Mech &m, const Batch &bt, int energy, int want_J, 
         e = cudaMallocAsync(reinterpret_cast<void **>(&Jg), sizeof(TJ) * size_t(n) * pitch_of(n) * L.grid, st);
         if (e != cudaSuccess) return set_error(PSR_E_OOM, "Jacobian slots for the block evaluator");
     }
-    block_eval_kernel<TJ><<<L.grid, kBT, L.smem, st>>>(m.dev, bt, energy, want_J, out, Jg);
+    block_eval_kernel<TJ><<<L.grid, kBT, L.smem, st>>>(m.dev, bt, energy, want_J, out, ro, Jg);
     e = cudaGetLastError();
     if (Jg) cudaFreeAsync(Jg, st);
     if (e != cudaSuccess) return cuda_error("block_eval_kernel launch", e);
     return PSR_OK;
 }
 
-int block_eval(const Mech &m, const Batch &bt, int energy, int want_J, int precision, double *out, cudaStream_t st) {
-    if (precision == PSR_MIXED && want_J) return block_eval_t<float>(m, bt, energy, want_J, out, st);
-    return block_eval_t<double>(m, bt, energy, want_J, out, st);
+int block_eval(const Mech &m, const Batch &bt, int energy, int want_J, int precision, double *out, cudaStream_t st,
+               RatesOut ro) {
+    if (precision == PSR_MIXED && want_J == 1) return block_eval_t<float>(m, bt, energy, want_J, out, st, ro);
+    return block_eval_t<double>(m, bt, energy, want_J, out, st, ro);
 }
 
 int block_adjoint(const Mech &m, const Batch &bt, int energy, const double *g, double *grad, double *lam_out,

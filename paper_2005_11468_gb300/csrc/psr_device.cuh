@@ -59,6 +59,12 @@ struct Batch {
     const int64_t *row_off;    // optional [B] start of reactor r's row in Y_in / Y0 / Y_out (else r K)
 };
 
+// Outputs of the rate evaluation (the paper's timed unit): [B][I] in mechanism-file order
+// and wdot [B][K]; any may be NULL.
+struct RatesOut {
+    double *kf, *kr, *q, *wdot;
+};
+
 // Start of reactor r's mass-fraction row.
 __device__ __forceinline__ int64_t row_of(const Batch &bt, int64_t r, int K) {
     return bt.row_off ? bt.row_off[r] : r * K;
@@ -91,6 +97,18 @@ template <>
 __device__ __forceinline__ double eff_v<double>(const DevMech &M, int e) { return __ldg(M.eff_val + e); }
 template <>
 __device__ __forceinline__ float eff_v<float>(const DevMech &M, int e) { return __ldg(M.eff_val_f + e); }
+
+// d/d[X_l] of one side's slot product given the products of the other two slots
+// (d0 = [X_s1][X_s2], ...): the sum over the slots that species l fills (mask bits 0..2).
+// The first slot is picked with selects (integer pipe); a species filling two slots adds
+// one term and only the three-slot case a second.
+__device__ __forceinline__ double slot_deriv(int m, double d0, double d1, double d2) {
+    const double first = (m & 1) ? d0 : ((m & 2) ? d1 : ((m & 4) ? d2 : 0.0));
+    const int rest = m & (m - 1);
+    double v = first + ((rest & 2) ? d1 : ((rest & 4) ? d2 : 0.0));
+    if (m == 7) v += d2;
+    return v;
+}
 
 // ---------------------------------------------------------------- thermo (NASA-7)
 __device__ __forceinline__ void nasa7(const double *__restrict__ nasa, int k, double T, double lnT, double invT,
@@ -153,7 +171,8 @@ __device__ __forceinline__ Troe troe_eval(const double *__restrict__ tp, double 
 int block_check(const Mech &m);
 int block_solve(const Mech &m, const Batch &bt, const Opts &o, int precision, bool fallback, int bps_req,
                 cudaStream_t st);
-int block_eval(const Mech &m, const Batch &bt, int energy, int want_J, int precision, double *out, cudaStream_t st);
+int block_eval(const Mech &m, const Batch &bt, int energy, int want_J, int precision, double *out, cudaStream_t st,
+               RatesOut ro = RatesOut{});
 int block_adjoint(const Mech &m, const Batch &bt, int energy, const double *g, double *grad, double *lam_out,
                   int32_t *ok, cudaStream_t st);
 int block_lu(int64_t B, int n, const double *A, const double *r, double *x, int32_t *ok, int precision,

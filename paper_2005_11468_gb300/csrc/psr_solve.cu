@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "psr_device.cuh"
 #include "psr_internal.h"
@@ -434,8 +435,8 @@ __device__ PSR_STAGE void eval_J(const DevMech &M, const WS<TJ> &w, const V2 &y,
             pl[t] = __ldg(pp + t);
             pnu[t] = TJ(__ldg(pn + t));
             const int fm = __ldg(pfm + t), rm = __ldg(prm + t);
-            const double dfl = ((fm & 1) ? d0 : 0.0) + ((fm & 2) ? d1 : 0.0) + ((fm & 4) ? d2 : 0.0);
-            const double drl = ((rm & 1) ? d3 : 0.0) + ((rm & 2) ? d4 : 0.0) + ((rm & 4) ? d5 : 0.0);
+            const double dfl = slot_deriv(fm, d0, d1, d2);
+            const double drl = slot_deriv(rm, d3, d4, d5);
             val[t] = TJ(Af * dfl - Ar * drl);
         }
         const TJ dqdM_t = TJ(dqdM);
@@ -1135,7 +1136,7 @@ __global__ void collect_unconverged(int64_t B, const int32_t *in_list, const int
 
 // residual / Jacobian at given states: one warp per state
 template <class TJ, bool SOOT>
-__global__ void eval_kernel(DevMech M, Batch bt, int energy, int want_J, double *out, size_t ws_per_warp) {
+__global__ void eval_kernel(DevMech M, Batch bt, int energy, int want_J, double *out, RatesOut ro, size_t ws_per_warp) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r = int64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
@@ -1174,6 +1175,18 @@ __global__ void eval_kernel(DevMech M, Batch bt, int energy, int want_J, double 
     const V2 zero{0.0, 0.0};
     V2 F, R;
     residual_R<TJ, SOOT>(cx, w, y, zero, y, F, R);
+    if (want_J == 2) {   // rates of the residual just evaluated: effective kf, kr, q_i, wdot_k
+        const int I = M.I;
+        for (int i = lane; i < I; i += 32) {
+            const int64_t o = r * I + __ldg(M.orig + i);
+            if (ro.kf) ro.kf[o] = w.kf[i];
+            if (ro.kr) ro.kr[o] = w.kr[i];
+            if (ro.q) ro.q[o] = w.q[i];
+        }
+        if (ro.wdot)
+            for (int j = lane; j < K; j += 32) ro.wdot[r * K + j] = w.v[j];
+        return;
+    }
     if (!want_J) {
         if (lane < n) out[r * n + lane] = F.a;
         if (lane + 32 < n) out[r * n + lane + 32] = F.b;
@@ -1414,7 +1427,8 @@ int launch_mixed(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int
 }
 
 template <class TJ, bool SOOT>
-int launch_eval_s(const Mech &m, const Batch &bt, int energy, int want_J, double *out, cudaStream_t st) {
+int launch_eval_s(const Mech &m, const Batch &bt, int energy, int want_J, double *out, cudaStream_t st,
+                  RatesOut ro) {
     const size_t wsb = ws_bytes<TJ>(m.K, m.I, m.K + 1 + m.dev.nsoot, m.n_troe, m.dev.nsoot);
     const int wpb = 2;
     const size_t smem = wpb * wsb;
@@ -1422,16 +1436,17 @@ int launch_eval_s(const Mech &m, const Batch &bt, int energy, int want_J, double
         cudaFuncSetAttribute(eval_kernel<TJ, SOOT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return cuda_error("cudaFuncSetAttribute", e);
     const int64_t grid = (bt.B + wpb - 1) / wpb;
-    eval_kernel<TJ, SOOT><<<unsigned(grid), wpb * 32, smem, st>>>(m.dev, bt, energy, want_J, out, wsb);
+    eval_kernel<TJ, SOOT><<<unsigned(grid), wpb * 32, smem, st>>>(m.dev, bt, energy, want_J, out, ro, wsb);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error("eval_kernel launch", e);
     return PSR_OK;
 }
 
 template <class TJ>
-int launch_eval(const Mech &m, const Batch &bt, int energy, int want_J, double *out, cudaStream_t st) {
-    if (m.dev.nsoot) return launch_eval_s<TJ, true>(m, bt, energy, want_J, out, st);
-    return launch_eval_s<TJ, false>(m, bt, energy, want_J, out, st);
+int launch_eval(const Mech &m, const Batch &bt, int energy, int want_J, double *out, cudaStream_t st,
+                RatesOut ro = RatesOut{}) {
+    if (m.dev.nsoot) return launch_eval_s<TJ, true>(m, bt, energy, want_J, out, st, ro);
+    return launch_eval_s<TJ, false>(m, bt, energy, want_J, out, st, ro);
 }
 
 // ---------------------------------------------------------------- allocation-free variant
@@ -1893,6 +1908,95 @@ int psr_batch_solve_multi(const psr_mech *const *mechs, int32_t n_mech, int64_t 
     }
     cudaFreeAsync(scr, st);
     return rc;
+}
+
+int psr_autotune(const psr_mech *m, int64_t B, const double *Y_in, const double *T_in, const double *tau,
+                 const double *P, const double *Y0, const double *T0, psr_options *opt, void *cuda_stream) {
+    int rc = check_mech(m);
+    if (rc) return rc;
+    if (!opt) return set_error(PSR_E_ARG, "psr_autotune: opt is NULL");
+    if ((rc = check_opts(opt))) return rc;
+    if (m->m.has_soot) return set_error(PSR_E_ARG, "psr_autotune: gas mechanisms only");
+    if (B < 1 || B > (int64_t(1) << 24)) return set_error(PSR_E_ARG, "psr_autotune: sample size out of 1..2^24");
+    if (!Y_in || !T_in || !tau || !P || !Y0 || !T0) return set_error(PSR_E_ARG, "psr_autotune: NULL pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const size_t nb = size_t(B), K = size_t(m->m.K);
+    char *buf = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&buf), nb * (K + 2) * 8 + nb * 4 * 4, st);
+    if (e != cudaSuccess) return set_error(PSR_E_OOM, "psr_autotune: output buffers");
+    double *Yo = reinterpret_cast<double *>(buf), *To = Yo + nb * K, *fn = To + nb;
+    int32_t *it = reinterpret_cast<int32_t *>(fn + nb), *ts = it + nb, *stt = ts + nb, *nf = stt + nb;
+    // candidates: warps per block x block cap on the warp path; the block path has one shape
+    struct Cand {
+        int wpb, bps;
+    };
+    std::vector<Cand> cands;
+    if (warp_path(m)) {
+        for (int w : {1, 2, 3, 4}) cands.push_back({w, 0});
+        for (int b : {2, 3, 4}) cands.push_back({2, b});
+    } else {
+        cands.push_back({0, 0});
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<int32_t> hs(nb);
+    double best_score = -1.0;
+    Cand best = cands[0];
+    psr_options trial = *opt;
+    rc = psr_batch_solve(m, B, Y_in, T_in, tau, P, Y0, T0, nullptr, Yo, To, it, ts, stt, fn, nf, &trial, st);
+    for (size_t c = 0; c < cands.size() && rc == PSR_OK; ++c) {
+        trial.warps_per_block = cands[c].wpb;
+        trial.blocks_per_sm = cands[c].bps;
+        cudaEventRecord(e0, st);
+        rc = psr_batch_solve(m, B, Y_in, T_in, tau, P, Y0, T0, nullptr, Yo, To, it, ts, stt, fn, nf, &trial, st);
+        cudaEventRecord(e1, st);
+        if (rc) break;
+        e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            rc = cuda_error("psr_autotune", e);
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        e = cudaMemcpy(hs.data(), stt, nb * 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            rc = cuda_error("psr_autotune status copy", e);
+            break;
+        }
+        int64_t conv = 0;
+        for (int32_t v : hs) conv += (v == PSR_CONVERGED || v == PSR_REFINE_FALLBACK);
+        const double score = ms > 0.f ? double(conv) / ms : 0.0;   // converged solves per ms
+        if (score > best_score) {
+            best_score = score;
+            best = cands[c];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(buf, st);
+    if (rc == PSR_OK) {
+        opt->warps_per_block = best.wpb;
+        opt->blocks_per_sm = best.bps;
+    }
+    return rc;
+}
+
+int psr_eval_rates(const psr_mech *m, int64_t B, const double *Y, const double *T, const double *P,
+                   const double *rate_mult, double *kf_out, double *kr_out, double *q_out, double *wdot_out,
+                   void *cuda_stream) {
+    int rc = check_mech(m);
+    if (rc) return rc;
+    if (m->m.has_soot) return set_error(PSR_E_ARG, "psr_eval_rates: gas mechanisms only");
+    if (B < 0) return set_error(PSR_E_ARG, "B < 0");
+    if (B == 0) return PSR_OK;
+    if (!Y || !T || !P) return set_error(PSR_E_ARG, "psr_eval_rates: NULL state pointer");
+    // the residual machinery runs with the state as its own inlet (the residual is discarded)
+    Batch bt{B, Y, T, P, P, Y, T, rate_mult, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    RatesOut ro{kf_out, kr_out, q_out, wdot_out};
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (!warp_path(m)) return block_eval(m->m, bt, PSR_FIXED_T, 2, PSR_FP64, nullptr, st, ro);
+    return launch_eval<double>(m->m, bt, PSR_FIXED_T, 2, nullptr, st, ro);
 }
 
 }  // extern "C"

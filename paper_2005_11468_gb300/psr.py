@@ -80,6 +80,8 @@ def lib():
         L.psr_batch_solve_soot.argtypes = [vp, i64] + [dp] * 9 + [dp] * 3 + [dp] * 5 + [ctypes.POINTER(COptions), vp]
         L.psr_eval_residual_soot.argtypes = [vp, i64] + [dp] * 9 + [dp, i32, vp]
         L.psr_eval_jacobian_soot.argtypes = [vp, i64] + [dp] * 9 + [dp, i32, i32, vp]
+        L.psr_eval_rates.argtypes = [vp, i64] + [dp] * 8 + [vp]
+        L.psr_autotune.argtypes = [vp, i64] + [dp] * 6 + [ctypes.POINTER(COptions), vp]
         L.psr_batch_solve_multi.argtypes = [ctypes.POINTER(vp), i32, i64, dp, dp] + [dp] * 8 + [dp] * 5 + \
             [ctypes.POINTER(COptions), vp]
         _lib = L
@@ -386,4 +388,37 @@ def batch_solve_multi(mechs, mech_id, row_off, Y_in, T_in, tau, P, Y0, T0, opts:
         _ptr(out["Y"], f64, (L,)), _ptr(out["T"], f64, (B,)), _ptr(out["iters"], i32, (B,)),
         _ptr(out["ts_steps"], i32, (B,)), _ptr(out["status"], i32, (B,)), _ptr(out["fnorm"], f64, (B,)),
         _ptr(out["nfev"], i32, (B,)), ctypes.byref(o), _stream()))
+    return out
+
+
+def autotune(mech: Mechanism, Y_in, T_in, tau, P, Y0, T0, opts: Options = None) -> Options:
+    """psr_autotune on a sample batch (torch CUDA tensors): returns a copy of `opts` with
+    the fastest launch shape (warps_per_block, blocks_per_sm) for this mechanism."""
+    import torch
+    f64 = torch.float64
+    B, K = Y_in.shape
+    base = opts or Options()
+    o = base.to_c()
+    _check(lib().psr_autotune(
+        mech.handle, B, _ptr(Y_in, f64, (B, K), "Y_in"), _ptr(T_in, f64, (B,), "T_in"), _ptr(tau, f64, (B,), "tau"),
+        _ptr(P, f64, (B,), "P"), _ptr(Y0, f64, (B, K), "Y0"), _ptr(T0, f64, (B,), "T0"), ctypes.byref(o),
+        _stream()))
+    return dataclasses.replace(base, warps_per_block=o.warps_per_block, blocks_per_sm=o.blocks_per_sm)
+
+
+def eval_rates(mech: Mechanism, Y, T, P, rate_mult=None, out=None):
+    """psr_eval_rates on torch CUDA tensors: dict kf, kr, q [B][I] (mechanism-file order)
+    and wdot [B][K]."""
+    import torch
+    f64 = torch.float64
+    B, K = Y.shape
+    dev = Y.device
+    if out is None:
+        out = dict(kf=torch.empty((B, mech.I), dtype=f64, device=dev), kr=torch.empty((B, mech.I), dtype=f64, device=dev),
+                   q=torch.empty((B, mech.I), dtype=f64, device=dev), wdot=torch.empty((B, K), dtype=f64, device=dev))
+    _check(lib().psr_eval_rates(
+        mech.handle, B, _ptr(Y, f64, (B, K), "Y"), _ptr(T, f64, (B,), "T"), _ptr(P, f64, (B,), "P"),
+        _ptr(rate_mult, f64, (mech.I,), "rate_mult"), _ptr(out.get("kf"), f64, (B, mech.I)),
+        _ptr(out.get("kr"), f64, (B, mech.I)), _ptr(out.get("q"), f64, (B, mech.I)),
+        _ptr(out.get("wdot"), f64, (B, K)), _stream()))
     return out

@@ -151,3 +151,41 @@ def test_graph_capture_replays_the_call(env):
     small = torch.tensor(mb["mech_id"] < 2, device=env["dev"])
     assert torch.equal(out["status"][small], eager["status"][small])
     assert torch.equal(out["T"][small], eager["T"][small])
+
+
+@pytest.mark.parametrize("cls", [0, 1])
+def test_uneven_batch_adjoint_matches_central_differences(env, cls):
+    """Adjoint gradients (torch.autograd over psr_batch_adjoint) of reactors of the uneven
+    batch's K = 10 and K = 53 classes against central differences (h = 1e-6 on ln m_i) of
+    tightly converged re-solves; the K = 200 class is checked against the oracle by
+    backward error in test_gpu_k200.py (its Jacobians are too ill-conditioned for
+    differences of re-solved roots)."""
+    import torch
+    from paper_2005_11468_gb300.autograd import psr_solve
+    mb = synth.mixed_batch(env["specs"], B=512)
+    bc = mb["batches"][cls].subset(range(3))
+    dev = env["dev"]
+    t = {k: torch.tensor(np.ascontiguousarray(getattr(bc, k)), dtype=torch.float64, device=dev)
+         for k in ("Y_in", "T_in", "tau", "P", "Y0", "T0")}
+    gm, spec = env["gms"][cls], env["specs"][cls]
+    tight = psr.Options(step_rtol=1e-13, step_atol_y=1e-18, step_atol_t=1e-12)
+    w = torch.tensor(np.random.Generator(np.random.PCG64(11 + cls)).standard_normal(spec.K), device=dev)
+    lnm = torch.zeros(spec.I, dtype=torch.float64, device=dev, requires_grad=True)
+    Y, T, st = psr_solve(lnm, gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"], tight)
+    ok = torch.isin(st, torch.tensor(psr.CONVERGED_STATES, device=dev, dtype=torch.int32))
+    assert ok.all()
+    loss = (Y * w).sum() + 1e-3 * T.sum()
+    loss.backward()
+    gr = lnm.grad.cpu().numpy()
+    h = 1e-6
+    Ys, Ts = Y.detach(), T.detach()
+    for i in np.random.Generator(np.random.PCG64(21 + cls)).choice(spec.I, 4, replace=False):
+        vals = []
+        for sgn in (+1, -1):
+            lp = torch.zeros(spec.I, dtype=torch.float64, device=dev)
+            lp[i] = sgn * h
+            o = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], Ys, Ts, rate_mult=torch.exp(lp),
+                                opts=tight)
+            vals.append(((o["Y"] * w).sum() + 1e-3 * o["T"].sum()).item())
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - gr[i]) <= 1e-4 * np.abs(gr).max() + 1e-4 * abs(gr[i]), (i, fd, gr[i])

@@ -274,3 +274,51 @@ def test_edge_cases(dev):
     with pytest.raises(psr.PsrError):
         psr.batch_solve(gm, s["Y_in"], s["T_in"], s["tau"], s["P"], s["Y0"], s["T0"], opts=psr.Options(ftol=-1))
 
+
+
+def test_autotune_picks_a_shape_with_identical_results(dev):
+    """psr_autotune returns one of its candidate launch shapes; solving with it gives the
+    default shape's results bit for bit (one warp per reactor either way)."""
+    import torch
+    _, mech, batch = workload("k53_b4096")
+    sub = batch.subset(range(1024))
+    t = to_dev(sub, dev)
+    gm = gpu_mech("k53_b4096")
+    base = psr.Options(precision=psr.PSR_MIXED)
+    tuned = psr.autotune(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"], base)
+    assert (tuned.warps_per_block, tuned.blocks_per_sm) in {(1, 0), (2, 0), (3, 0), (4, 0), (2, 2), (2, 3), (2, 4)}
+    assert tuned.precision == base.precision and tuned.ftol == base.ftol
+    a = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"], opts=base)
+    b = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"], opts=tuned)
+    assert torch.equal(a["Y"], b["Y"]) and torch.equal(a["status"], b["status"])
+    with pytest.raises(psr.PsrError):
+        psr.autotune(gm, t["Y_in"][:0], t["T_in"][:0], t["tau"][:0], t["P"][:0], t["Y0"][:0], t["T0"][:0])
+
+
+@pytest.mark.parametrize("name", ["k53_b4096", "k200_b2048"])
+def test_eval_rates_match_oracle(dev, name):
+    """psr_eval_rates (the paper's timed unit: k_f, K_c -> k_r, q, wdot) against the
+    oracle's Eqs. (4)-(9) at seeded states, on the warp (K = 53) and block (K = 200) paths."""
+    import torch
+    _, mech, batch = workload(name)
+    m = 8
+    X = random_states(mech, m, seed=31)
+    P = np.full(m, synth.ONE_ATM)
+    gm = gpu_mech(name)
+    lnm = np.random.Generator(np.random.PCG64(4)).uniform(-0.3, 0.3, mech.I)
+    out = psr.eval_rates(gm, torch.tensor(X[:, :-1], device=dev), torch.tensor(X[:, -1], device=dev),
+                         torch.tensor(P, device=dev), rate_mult=torch.tensor(np.exp(lnm), device=dev))
+    kf, kr, q, wd = (out[k].cpu().numpy() for k in ("kf", "kr", "q", "wdot"))
+    T = X[:, -1]
+    _, rho, C = O.mixture_state(mech, X[:, :-1], T, P)
+    q_o = O.rates_of_progress(mech, T, C, lnmult=lnm)
+    wd_o = O.net_production_rates(mech, q_o)
+    kf_o = O.forward_rate_constants(mech, T)
+    Kc_o = O.equilibrium_constants(mech, T)
+    plain = ~mech.is_troe
+    np.testing.assert_allclose(kf[:, plain], kf_o[:, plain], rtol=1e-12)
+    np.testing.assert_allclose(kf / kr, np.broadcast_to(Kc_o, kf.shape), rtol=1e-10)
+    gross = np.abs(q_o).max(axis=1, keepdims=True)
+    assert np.max(np.abs(q - q_o) / gross) <= 1e-11
+    scale = (np.abs(q_o) @ np.abs(mech.nu.T)).max(axis=1, keepdims=True)
+    assert np.max(np.abs(wd - wd_o) / scale) <= 1e-11
