@@ -448,17 +448,12 @@ __device__ __forceinline__ void pivot_candidate(TJ v, int row, unsigned long lon
 
 template <class TJ>
 __device__ __forceinline__ void warp_argmax(unsigned long long &best, TJ &bv, int &bi) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long ob = __shfl_xor_sync(kFull, best, o);
-        const TJ ov = __shfl_xor_sync(kFull, bv, o);
-        const int oi = __shfl_xor_sync(kFull, bi, o);
-        if (ob > best || (ob == best && oi < bi)) {
-            best = ob;
-            bv = ov;
-            bi = oi;
-        }
-    }
+    using Key = decltype(abs_key(TJ(0)));
+    const int win = warp_argmax_row(Key(best), bi);               // hardware integer reductions
+    const int src = __ffs(__ballot_sync(kFull, bi == win)) - 1;    // the lane holding that row
+    best = __shfl_sync(kFull, best, src);
+    bv = __shfl_sync(kFull, bv, src);
+    bi = win;
 }
 
 constexpr int kNB = 32;                  // panel width of the blocked LU

@@ -40,6 +40,19 @@ __device__ __forceinline__ unsigned long long abs_key(double v) {
     return static_cast<unsigned long long>(__double_as_longlong(v)) & 0x7fffffffffffffffull;
 }
 __device__ __forceinline__ bool key_is_finite_nonzero(uint32_t k) { return k != 0u && k < 0x7f800000u; }
+
+// Warp arg-max of pivot keys with the hardware integer reductions: the largest key, ties
+// to the smallest row (rows of lanes without a candidate are >= any real row).
+__device__ __forceinline__ int warp_argmax_row(uint32_t key, int row) {
+    const uint32_t m = __reduce_max_sync(kFull, key);
+    return int(__reduce_min_sync(kFull, key == m ? uint32_t(row) : 0xffffffffu));
+}
+__device__ __forceinline__ int warp_argmax_row(unsigned long long key, int row) {
+    const uint32_t hi = uint32_t(key >> 32), lo = uint32_t(key);
+    const uint32_t mh = __reduce_max_sync(kFull, hi);
+    const uint32_t ml = __reduce_max_sync(kFull, hi == mh ? lo : 0u);
+    return int(__reduce_min_sync(kFull, (hi == mh && lo == ml) ? uint32_t(row) : 0xffffffffu));
+}
 __device__ __forceinline__ bool key_is_finite_nonzero(unsigned long long k) {
     return k != 0ull && k < 0x7ff0000000000000ull;
 }

@@ -658,16 +658,7 @@ __device__ PSR_STAGE bool lu_factor(const WS<TJ> &w, int n) {
                 bi = i;
             }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const auto ob = __shfl_xor_sync(kFull, best, o);
-            const int oi = __shfl_xor_sync(kFull, bi, o);
-            if (ob > best || (ob == best && oi < bi)) {
-                best = ob;
-                bi = oi;
-            }
-        }
-        const int p = bi;
+        const int p = min(warp_argmax_row(best, bi), n);
         const TJ pv = (p < n) ? w.J[size_t(p) * P + k] : TJ(0);
         __syncwarp();   // every lane has read the pivot before the row swap overwrites it
         if (!key_is_finite_nonzero(abs_key(pv))) return false;
@@ -692,13 +683,15 @@ __device__ PSR_STAGE bool lu_factor(const WS<TJ> &w, int n) {
             const TJ l = ri[k] * inv;
             ri[k] = l;
             int j = k + 1;
-            for (; j + 3 < n; j += 4) {
-                const TJ a0 = ri[j], a1 = ri[j + 1], a2 = ri[j + 2], a3 = ri[j + 3];
-                const TJ b0 = rk[j], b1 = rk[j + 1], b2 = rk[j + 2], b3 = rk[j + 3];
-                ri[j] = fma(-l, b0, a0);
-                ri[j + 1] = fma(-l, b1, a1);
-                ri[j + 2] = fma(-l, b2, a2);
-                ri[j + 3] = fma(-l, b3, a3);
+            for (; j + 7 < n; j += 8) {   // loads batched ahead of the stores
+                TJ a[8], b[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    a[u] = ri[j + u];
+                    b[u] = rk[j + u];
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) ri[j + u] = fma(-l, b[u], a[u]);
             }
             for (; j < n; ++j) ri[j] = fma(-l, rk[j], ri[j]);
         }
