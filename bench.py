@@ -195,6 +195,18 @@ def run_reference(args):
     if rank != 0:
         return
     K, W = args.steps, args.warmup
+    if args.workload == RATES:
+        from paper_2005_11468_gb300 import synth
+        tc = oracle_rates_time(synth.workload_mechanism(RATES), 20000)
+        v = 1.0 / tc
+        print(json.dumps({"impl": "reference", "metric": RATES_METRIC, "value": v, "unit": "states/s",
+                          "n_gpus": args.gpus, "steps": K, "warmup": W, "ms_per_step": 1e3 * tc * 20000,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": {"workload": f"{RATES} (20000 states, vectorised oracle)"},
+                          "cpu_baseline": {"value": v, "unit": "states/s", "cores": 1, "kind": "oracle",
+                                           "sample": "20000 states"},
+                          "e2e": {"value": v, "unit": "states/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
     if args.workload == MIXED:
         v, detail = oracle_time_mixed((2, 1, 1))
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
@@ -585,12 +597,123 @@ def run_multi(args):
         pg.destroy_process_group()
 
 
+RATES = "k101_rates"   # the paper's timed unit: one rate evaluation per state
+RATES_METRIC = "rate evaluations/s (kf, kr, q, wdot per state; Eqs. (4)-(9)) at T = 1800 K"
+
+
+def _rate_states(spec, B, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    Y = rng.dirichlet(np.full(spec.K, 0.7), size=B)
+    return Y, np.full(B, 1800.0), np.full(B, 101325.0 * 10.0)
+
+
+def oracle_rates_time(spec, B):
+    """Seconds per state of the oracle's vectorised rate functions (one core)."""
+    import warnings
+    from oracle import psr_oracle as O
+    from paper_2005_11468_gb300 import synth
+    warnings.filterwarnings("ignore", category=RuntimeWarning)
+    mech = O.Mechanism(synth.mechanism_text(spec))
+    Y, T, P = _rate_states(spec, B, 7)
+    t0 = time.perf_counter()
+    _, _, C = O.mixture_state(mech, Y, T, P)
+    q = O.rates_of_progress(mech, T, C)
+    O.net_production_rates(mech, q)
+    return (time.perf_counter() - t0) / B
+
+
+def run_rates(args):
+    """Rate evaluation (psr_eval_rates) of a 101-species / 542-reaction synthetic mechanism
+    at B = 1e2 ... 1e6 states, T = 1800 K, the unit the paper times on its GPU; the value
+    is states/s at the largest batch, timed with the states resident."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2005_11468_gb300 import _build, psr, synth
+    if not os.path.exists(psr.LIB_PATH):
+        _build.build()
+    spec = synth.workload_mechanism(RATES)
+    mech = psr.Mechanism(synth.mechanism_text(spec))
+    K, W = args.steps, args.warmup
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    per_b, ms_big, B_big = {}, 0.0, 0
+    sampler = ClockSampler(local)
+    for B in (100, 1000, 10000, 100000, 1000000):
+        Y, T, P = _rate_states(spec, B, 1 + rank)
+        d = dict(Y=torch.tensor(Y, device=dev), T=torch.tensor(T, device=dev), P=torch.tensor(P, device=dev))
+        out = dict(q=torch.empty((B, spec.I), dtype=torch.float64, device=dev),
+                   wdot=torch.empty((B, spec.K), dtype=torch.float64, device=dev))
+        for _ in range(W):
+            psr.eval_rates(mech, d["Y"], d["T"], d["P"], out=out)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        ctx = sampler if B == 1000000 else _Null()
+        with ctx:
+            for s in range(K):
+                flush.fill_(float(s))
+                ev[s][0].record(stream)
+                psr.eval_rates(mech, d["Y"], d["T"], d["P"], out=out)
+                ev[s][1].record(stream)
+            torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / K
+        per_b[B] = B / (ms / 1e3)
+        ms_big, B_big = ms, B
+        del d, out
+    # end to end at B = 1e5: states from pinned host memory, rates back to the host
+    B = 100000
+    Y, T, P = _rate_states(spec, B, 1 + rank)
+    host = dict(Y=torch.tensor(Y).pin_memory(), T=torch.tensor(T).pin_memory(), P=torch.tensor(P).pin_memory())
+    hq = torch.empty((B, spec.I), dtype=torch.float64).pin_memory()
+    hw = torch.empty((B, spec.K), dtype=torch.float64).pin_memory()
+    d = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+    out = dict(q=torch.empty((B, spec.I), dtype=torch.float64, device=dev),
+               wdot=torch.empty((B, spec.K), dtype=torch.float64, device=dev))
+    e_t = 0.0
+    for s in range(K):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in d:
+            d[k].copy_(host[k], non_blocking=True)
+        psr.eval_rates(mech, d["Y"], d["T"], d["P"], out=out)
+        hq.copy_(out["q"], non_blocking=True)
+        hw.copy_(out["wdot"], non_blocking=True)
+        torch.cuda.synchronize()
+        e_t += time.perf_counter() - t0
+    value = per_b[B_big]
+    work = spec.I * (20 + 2 * EXP_FLOPS) + spec.K * 45 + (spec.n_troe) * (4 * EXP_FLOPS + 2 * LOG_FLOPS + 30)
+    achieved = work * value / 1e12
+    line = {"metric": RATES_METRIC, "value": value, "unit": "states/s", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms_big, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{RATES}: K={spec.K}, I={spec.I} ({spec.n_tb} third-body, {spec.n_troe} Troe), "
+                                   f"B={B_big} states at T=1800 K, outputs q and wdot",
+                       "l2": "flushed (256 MB write) between timed steps"},
+            "states_per_s_by_batch": {str(b): v for b, v in per_b.items()},
+            "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "work_model": "per state: I (20 + 2 exp) + 45 K + Troe terms, exp=40 flop slots"},
+            "e2e": {"value": B * K / e_t, "unit": "states/s", "h2d_bytes_per_step": B * (spec.K + 2) * 8,
+                    "d2h_bytes_per_step": B * (spec.I + spec.K) * 8},
+            "gpu_launches": K * 5, "clocks": sampler.summary()}
+    if not args.no_cpu_baseline:
+        tc = oracle_rates_time(spec, 20000)
+        line["cpu_baseline"] = {"value": 1.0 / tc, "unit": "states/s", "cores": 1, "kind": "oracle",
+                                "sample": "20000 states, the oracle's vectorised numpy rate functions"}
+        line["gpu_over_oracle_by_batch"] = {str(b): v * tc for b, v in per_b.items()}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == MIXED:
         run_multi(args)
+    elif args.workload == RATES:
+        run_rates(args)
     else:
         run_ours(args)
 

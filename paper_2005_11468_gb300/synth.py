@@ -406,6 +406,9 @@ WORKLOADS = {
     "k53soot_b16384": dict(K=53, I=325, n_tb=10, n_troe=15, B=16384, soot=True, tag=3,
                            tau_range=(1e-5, 1e-1)),
     "k200_b2048": dict(K=200, I=1500, n_tb=60, n_troe=40, B=2048, soot=False, tag=4),
+    # the size of the ethylene mechanism the paper times its rate kernel on (101 species,
+    # 542 reactions), for the rate-evaluation measurement
+    "k101_rates": dict(K=101, I=542, n_tb=20, n_troe=20, B=100000, soot=False, tag=6),
 }
 # uneven batch: 50/35/15 % of reactors from the K=10 / K=53 / K=200 mechanisms
 MIXED_WORKLOAD = dict(B=32768, parts=("k10_b64", "k53_b4096", "k200_b2048"),

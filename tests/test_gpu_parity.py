@@ -322,3 +322,33 @@ def test_eval_rates_match_oracle(dev, name):
     assert np.max(np.abs(q - q_o) / gross) <= 1e-11
     scale = (np.abs(q_o) @ np.abs(mech.nu.T)).max(axis=1, keepdims=True)
     assert np.max(np.abs(wd - wd_o) / scale) <= 1e-11
+
+
+def test_fixed_t_sweep_with_continuation(dev):
+    """The paper's run mode: a fixed-T grid (1500-2000 K in 50 K steps x tau 5-95 ms in
+    5 ms steps) solved column by column with the previous temperature's roots as guesses.
+    Warm and cold starts reach the same roots where both converge on the same branch,
+    continuation needs fewer Newton iterations in all, and two grid points match the
+    oracle."""
+    from paper_2005_11468_gb300 import sweep
+    spec, mech, batch = workload("k53_b4096")
+    gm = gpu_mech("k53_b4096")
+    Y_in = batch.Y_in[0]
+    T_grid = np.arange(1500.0, 2001.0, 50.0)
+    tau_grid = np.arange(5e-3, 95.1e-3, 5e-3)
+    Yw, sw, iw = sweep.fixed_t_sweep(gm, Y_in, T_grid, tau_grid, warm=True)
+    Yc, sc, ic = sweep.fixed_t_sweep(gm, Y_in, T_grid, tau_grid, warm=False)
+    cw, cc = np.isin(sw, psr.CONVERGED_STATES), np.isin(sc, psr.CONVERGED_STATES)
+    assert cw.mean() >= 0.95 and cc.mean() >= 0.95
+    both = cw & cc
+    big = Yc > Y_MIN
+    rel = np.where(big, np.abs(Yw - Yc) / np.where(big, Yc, 1.0), 0.0).max(axis=2)
+    assert np.mean(rel[both] <= Y_REL) >= 0.95     # other points sit on another root (a valid one)
+    assert iw[both].sum() < ic[both].sum()
+    for a, j in ((0, 0), (len(T_grid) - 1, len(tau_grid) - 1)):
+        inlet = O.Inlet(Y_in, 300.0, tau_grid[j], synth.ONE_ATM)
+        inlet.T_spec = T_grid[a]
+        r = O.solve_reactor(mech, inlet, np.r_[Y_in, T_grid[a]], energy="fixed")
+        assert r.status == O.CONVERGED
+        big = r.x[:-1] > Y_MIN
+        assert np.max(np.abs(Yc[a, j][big] - r.x[:-1][big]) / r.x[:-1][big]) <= Y_REL
