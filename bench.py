@@ -252,7 +252,8 @@ def run_ours(args):
     w = synth.WORKLOADS[args.workload]
     spec = synth.workload_mechanism(args.workload)
     mech = psr.Mechanism(synth.mechanism_text(spec))
-    batch = synth.make_batch(spec, w["B"], seed=synth.MECH_SEED_BASE + 10 * w["tag"] + 1 + 1000 * rank,
+    from paper_2005_11468_gb300 import shard
+    batch = synth.make_batch(spec, w["B"], seed=shard.shard_seed(synth.MECH_SEED_BASE + 10 * w["tag"] + 1, rank),
                              tau_range=w.get("tau_range", (1e-4, 1e-2)))
     t = {k: torch.tensor(getattr(batch, k), dtype=torch.float64, device=dev)
          for k in ("Y_in", "T_in", "tau", "P", "Y0", "T0")}
@@ -296,11 +297,7 @@ def run_ours(args):
         conv = int(np.isin(st, psr.CONVERGED_STATES).sum())
         nfev = out["nfev"].cpu().numpy()
         iters = out["iters"].cpu().numpy()
-        total = sum(ms)
-        if pg is not None:
-            tt = torch.tensor([total], dtype=torch.float64, device=dev)
-            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-            total = tt.item()
+        total = shard.reduce_max(pg, [sum(ms)], dev)[0]   # the slowest rank's time
         return dict(ms=ms, total_ms=total, conv=conv, nfev=nfev, iters=iters)
 
     K, W = args.steps, args.warmup
@@ -334,22 +331,16 @@ def run_ours(args):
                              opts=eopts, out=hout)
         e_t += time.perf_counter() - t0
         e_conv += int(np.isin(hout["status"], psr.CONVERGED_STATES).sum())
-    if pg is not None:
-        tt = torch.tensor([e_t], dtype=torch.float64, device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        e_t = tt.item()
+    e_t = shard.reduce_max(pg, [e_t], dev)[0]
     h2d = B * spec.K * 8 * 2 + B * 8 * 4
     d2h = B * spec.K * 8 + B * 8 * 2 + B * 4 * 4
 
     conv_all = mixed["conv"] * K
     conv64 = fp64["conv"] * len(fp64["ms"])
-    if pg is not None:
-        c = torch.tensor([conv_all, conv64, e_conv], dtype=torch.float64, device=dev)
-        pg.all_reduce(c)
-        conv_all, conv64, e_conv = (float(x) for x in c.tolist())
-    value = conv_all / (mixed["total_ms"] / 1e3)
-    value64 = conv64 / (fp64["total_ms"] / 1e3)
-    e2e_value = e_conv / e_t
+    conv_all, conv64, e_conv = shard.reduce_sum(pg, [conv_all, conv64, e_conv], dev)
+    value = shard.job_throughput(conv_all, mixed["total_ms"] / 1e3)
+    value64 = shard.job_throughput(conv64, fp64["total_ms"] / 1e3)
+    e2e_value = shard.job_throughput(e_conv, e_t)
 
     if rank != 0:
         if pg is not None:
@@ -474,7 +465,9 @@ def run_multi(args):
         _build.build()
     specs = [synth.workload_mechanism(nm) for nm in synth.MIXED_WORKLOAD["parts"]]
     gms = [psr.Mechanism(synth.mechanism_text(sp)) for sp in specs]
-    mb = synth.mixed_batch(specs, seed=synth.MECH_SEED_BASE + 10 * synth.MIXED_WORKLOAD["tag"] + 1 + 1000 * rank)
+    from paper_2005_11468_gb300 import shard
+    mb = synth.mixed_batch(specs, seed=shard.shard_seed(synth.MECH_SEED_BASE + 10 * synth.MIXED_WORKLOAD["tag"] + 1,
+                                                        rank))
     B = len(mb["mech_id"])
     keys = ("Y_in", "Y0", "T_in", "tau", "P", "T0")
     host = {k: torch.tensor(mb[k], dtype=torch.float64).pin_memory() for k in keys}
