@@ -47,7 +47,9 @@ extern "C" {
 #define PSR_MAX_ITER 1      /* max_newton Newton iterations used */
 #define PSR_NONFINITE 2     /* the residual at the initial guess is not finite */
 #define PSR_TS_EXHAUSTED 4  /* max_ts_rounds time-stepping rounds, or dt collapsed */
-#define PSR_BAD_INPUT 7      /* psr_batch_solve_multi: mechanism id out of range, not solved */
+#define PSR_BAD_INPUT 7
+#define PSR_JAC_ANALYTIC 0
+#define PSR_JAC_FD 1      /* psr_batch_solve_multi: mechanism id out of range, not solved */
 #define PSR_REFINE_FALLBACK 5 /* PSR_MIXED: converged (same criterion) after the FP32-Jacobian
                                  launch left it unconverged and the FP64 re-solve succeeded */
 
@@ -103,7 +105,9 @@ typedef struct {
     int32_t warps_per_block;/* 0 = default (2); at most 4 */
     int32_t blocks_per_sm;  /* 0 = as many as fit */
     int32_t mixed_fallback; /* 1 (default): PSR_MIXED re-solves unconverged reactors in FP64 */
-    int32_t reserved[6];
+    int32_t jacobian;       /* PSR_JAC_ANALYTIC (default) or PSR_JAC_FD: central differences
+                               as the paper builds it (Sec. 1), K + 1 <= 64 gas mechanisms */
+    int32_t reserved[5];
 } psr_options;
 
 void psr_options_default(psr_options *o);
@@ -203,6 +207,16 @@ int psr_batch_solve_multi(const psr_mech *const *mechs, int32_t n_mech, int64_t 
                           const double *Y0, const double *T0, double *Y_out, double *T_out,
                           int32_t *iters, int32_t *ts_steps, int32_t *status, double *fnorm,
                           int32_t *nfev, const psr_options *opt, void *cuda_stream);
+
+/* Jacobian by central differences, the paper's construction (Sec. 1): column j from
+ * residuals at x +- h_j e_j, h_j = 1e-6 max(|x_j|, s_j) with s = 0.1 for mass fractions and
+ * 1000 K for T; the mass-fraction columns reuse the state's rate constants (they depend
+ * on T only, Sec. 3). Arguments and layout as psr_eval_jacobian (FP64). Gas mechanisms
+ * with K + 1 <= 64; PSR_E_UNSUPPORTED otherwise. */
+int psr_eval_jacobian_fd(const psr_mech *m, int64_t B,
+                         const double *Y_in, const double *T_in, const double *tau, const double *P,
+                         const double *Y, const double *T, const double *rate_mult, double *J_out,
+                         int32_t energy, void *cuda_stream);
 
 /* Autotuner for the launch shape (the paper has no counterpart; a service of the
  * library): solves the caller's sample batch (device arrays as psr_batch_solve, B >= 1,

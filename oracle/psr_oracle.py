@@ -437,7 +437,7 @@ def jacobian_cs(system, x, h=1e-30):
     return (system.F(X).imag / h).T
 
 
-def _damped_newton(system, x, c, x_ref, max_it, opts, steady, counter):
+def _damped_newton(system, x, c, x_ref, max_it, opts, steady, counter, fnorm=None):
     """Damped Newton on R(y) = F(y) + c (y - x_ref) from y = x (c = 0: the steady
     problem; c = tau/dt D^-1: one backward-Euler step of dx/dt = -D F / tau).
 
@@ -448,9 +448,19 @@ def _damped_newton(system, x, c, x_ref, max_it, opts, steady, counter):
     than dy in the scaled max-norm (species absolute, temperature relative).
     Steady: converged when ||F||_inf <= ftol and the undamped step is below the
     polish tolerance; that step is applied. Time step: converged when the undamped
-    step is below ts_rtol. Returns (y, F(y), converged)."""
+    step is below ts_rtol. Returns (y, F(y), converged); fnorm, when given, receives
+    ||F||_inf (the steady residual, not R) at the first and at the last evaluated point."""
+    def residual(v):
+        Fv = system.F(v)[0]
+        if fnorm is not None:
+            f = float(np.max(np.abs(Fv)))
+            if fnorm[0] is None:
+                fnorm[0] = f
+            fnorm[1] = f
+        return Fv + c * (v - x_ref)
+
     y = x.copy()
-    R = system.F(y)[0] + c * (y - x_ref)
+    R = residual(y)
     dn_prev = math.inf
     for _ in range(max_it):
         if counter[0] >= opts.max_newton:
@@ -480,7 +490,7 @@ def _damped_newton(system, x, c, x_ref, max_it, opts, steady, counter):
         for _ in range(opts.max_damp):
             yt = y + lam * dy
             if system.in_bounds(yt, opts):
-                Rt = system.F(yt)[0] + c * (yt - x_ref)
+                Rt = residual(yt)
                 if np.all(np.isfinite(Rt)):
                     dbar = lu_solve(LU, piv, -Rt)
                     if float(np.max(np.abs(dbar) * w)) < dn:
@@ -498,10 +508,12 @@ def solve_system(system, x0, opts: Options = Options()):
     iteration on the steady problem; when it fails (damping exhausted, corrections
     not shrinking, singular J) the estimate it started from is conditioned by
     ts_steps backward-Euler steps of the transient form dx/dt = -D F(x) / tau, each
-    solved by damped Newton; dt grows by 2 after a step solved in <= 3 iterations
-    (1.25 after 4, 1 after more) and shrinks by dt_shrink after a failed one; then
-    Newton is tried again. iters counts every Newton iteration (one Jacobian and LU
-    each), ts_steps the accepted pseudo-time steps."""
+    solved by damped Newton; after an accepted step dt grows by 2 if the step took
+    <= 3 iterations (1.25 after 4, 1 after more), times the factor by which the step
+    reduced ||F||_inf, clipped to [1, 4] (switched evolution relaxation, Mulder & van
+    Leer 1985; ||F||_inf taken at the last point each Newton evaluated), and shrinks by
+    dt_shrink after a failed step; then Newton is tried again. iters counts every
+    Newton iteration (one Jacobian and LU each), ts_steps the accepted pseudo-time steps."""
     tau = system.inlet.tau
     x = np.array(x0, dtype=np.float64)
     F = system.F(x)[0]
@@ -512,7 +524,8 @@ def solve_system(system, x0, opts: Options = Options()):
     dt = opts.dt0_over_tau * tau
     zero = np.zeros(system.n)
     while True:
-        y, Fy, conv = _damped_newton(system, x, zero, x, opts.max_newton, opts, True, counter)
+        fn = [None, None]
+        y, Fy, conv = _damped_newton(system, x, zero, x, opts.max_newton, opts, True, counter, fn)
         if conv:
             return Result(y, CONVERGED, counter[0], ts, float(np.max(np.abs(Fy))))
         if counter[0] >= opts.max_newton:
@@ -523,10 +536,12 @@ def solve_system(system, x0, opts: Options = Options()):
         if rounds > opts.max_ts_rounds:
             return Result(x, TS_EXHAUSTED, counter[0], ts, float(np.max(np.abs(system.F(x)[0]))))
         taken = 0
+        f_prev = fn[0]                      # ||F(x)||_inf of the estimate being conditioned
         while taken < opts.ts_steps:
             c = tau / dt * system.transient_weights(x)
             used = counter[0]
-            y, Fy, conv = _damped_newton(system, x, c, x, opts.ts_newton, opts, False, counter)
+            fs = [None, None]
+            y, Fy, conv = _damped_newton(system, x, c, x, opts.ts_newton, opts, False, counter, fs)
             used = counter[0] - used
             if counter[0] >= opts.max_newton:
                 return Result(x, MAX_ITER, counter[0], ts, float(np.max(np.abs(system.F(x)[0]))))
@@ -534,8 +549,11 @@ def solve_system(system, x0, opts: Options = Options()):
                 x = y
                 taken += 1
                 ts += 1
-                # grow dt by how easily the step was solved
+                # grow dt by how easily the step was solved and how much it reduced ||F||
                 g = 2.0 if used <= 3 else (1.25 if used == 4 else 1.0)
+                if fs[1] is not None and fs[1] > 0.0 and f_prev is not None:
+                    g *= min(4.0, max(1.0, f_prev / fs[1]))
+                f_prev = fs[1]
                 dt = min(g * dt, 1e6 * tau)
             else:
                 dt *= opts.dt_shrink

@@ -536,6 +536,7 @@ void psr_options_default(psr_options *o) {
     o->precision = PSR_FP64;
     o->energy = PSR_ADIABATIC;
     o->mixed_fallback = 1;
+    o->jacobian = PSR_JAC_ANALYTIC;
 }
 
 }  // extern "C"

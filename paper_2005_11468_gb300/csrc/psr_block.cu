@@ -775,11 +775,13 @@ __device__ void b_residual_R(BCtx &cx, const BWS<TJ> &w, const double *y, const 
 // stop, bounds; steady mode converges on ||R||_inf <= ftol plus a small last step.
 template <class TJ>
 __device__ bool b_damped_newton(BCtx &cx, const BWS<TJ> &w, double *y, const double *xref, const double *c,
-                                int max_it, bool steady, int &counter) {
+                                int max_it, bool steady, int &counter, double *fnorm) {
     const int t = threadIdx.x;
     const int K = cx.K, n = cx.n;
     const Opts &o = cx.o;
     b_residual_R(cx, w, y, c, xref, w.F, w.R);
+    // ||F||_inf of the steady residual at the first and the last evaluated point
+    if (fnorm) fnorm[0] = fnorm[1] = bmax(t < n ? fabs(w.F[t]) : 0.0, w.red);
     double dn_prev = INFINITY;
     for (int it = 0; it < max_it; ++it) {
         if (counter >= o.max_newton) break;
@@ -810,6 +812,7 @@ __device__ bool b_damped_newton(BCtx &cx, const BWS<TJ> &w, double *y, const dou
             __syncthreads();
             if (b_in_bounds(w.yt, K, o)) {
                 b_residual_R(cx, w, w.yt, c, xref, w.F, w.Rt);
+                if (fnorm) fnorm[1] = bmax(t < n ? fabs(w.F[t]) : 0.0, w.red);
                 if (b_all_finite(w.Rt, n)) {
                     b_lu_solve_neg(w, n, w.Rt, w.db);
                     if (b_scaled_max(w.db, y, K, n, w.red) < dn) {
@@ -880,7 +883,8 @@ __device__ void b_solve_one(BCtx &cx, const BWS<TJ> &w, const Batch &bt, int64_t
                 w.c[t] = 0.0;
             }
             __syncthreads();
-            const bool conv = b_damped_newton(cx, w, w.y, w.x, w.c, o.max_newton, true, counter);
+            double fn[2];
+            const bool conv = b_damped_newton(cx, w, w.y, w.x, w.c, o.max_newton, true, counter, fn);
             if (conv) {
                 status = PSR_CONVERGED;
                 out = w.y;
@@ -899,6 +903,7 @@ __device__ void b_solve_one(BCtx &cx, const BWS<TJ> &w, const Batch &bt, int64_t
             }
             int taken = 0;
             bool done = false;
+            double f_prev = fn[0];   // ||F(x)||_inf of the estimate being conditioned
             while (taken < o.ts_steps) {
                 const double Tx = w.x[K];
                 const double s = tau / dt;
@@ -910,7 +915,8 @@ __device__ void b_solve_one(BCtx &cx, const BWS<TJ> &w, const Batch &bt, int64_t
                 }
                 __syncthreads();
                 const int used0 = counter;
-                const bool ok = b_damped_newton(cx, w, w.y, w.x, w.c, o.ts_newton, false, counter);
+                double fs[2];
+                const bool ok = b_damped_newton(cx, w, w.y, w.x, w.c, o.ts_newton, false, counter, fs);
                 const int used = counter - used0;
                 if (counter >= o.max_newton) {
                     status = PSR_MAX_ITER;
@@ -923,7 +929,11 @@ __device__ void b_solve_one(BCtx &cx, const BWS<TJ> &w, const Batch &bt, int64_t
                     __syncthreads();
                     ++taken;
                     ++ts;
-                    const double g = (used <= 3) ? 2.0 : (used == 4 ? 1.25 : 1.0);
+                    // growth by how easily the step was solved, times its reduction of ||F||
+                    // clipped to [1, 4] (switched evolution relaxation)
+                    double g = (used <= 3) ? 2.0 : (used == 4 ? 1.25 : 1.0);
+                    if (fs[1] > 0.0) g *= fmin(4.0, fmax(1.0, f_prev / fs[1]));
+                    f_prev = fs[1];
                     dt = fmin(g * dt, 1e6 * tau);
                 } else {
                     dt *= o.dt_shrink;

@@ -87,6 +87,7 @@ struct Opts {
     double ftol, step_rtol, step_atol_y, step_atol_t, ts_rtol, ts_atol_y, dt0_over_tau, dt_shrink,
         y_floor, t_min, t_max;
     int max_newton, max_damp, max_ts_rounds, ts_steps, ts_newton, energy;
+    int jac_fd;   // Jacobian by central differences (the paper's method) instead of analytic
 };
 
 // Scalars of the last residual evaluation that the Jacobian reuses.

@@ -174,7 +174,10 @@ __device__ __forceinline__ void soot_eval(const double *__restrict__ st, const d
 // ---------------------------------------------------------------- residual, Eqs. (2)-(9)
 // Evaluates F at state y; leaves C, hRT, gS, kf, kr (effective) of this state in shared
 // memory and the scalars/lane data in mx/sl for the Jacobian.
-template <class TJ, bool SOOT>
+// FRZ: a perturbation of the mass fractions at the temperature of the previous (full)
+// evaluation: thermo, k_f and k_r of elementary and third-body reactions are reused from
+// the caches (rate constants depend on T only); falloff rows are recomputed ([M] moves).
+template <class TJ, bool SOOT, bool FRZ = false>
 __device__ PSR_STAGE void eval_F(const DevMech &M, const WS<TJ> &w, const V2 &y, V2 &F, Mix &mx, SpecLane &sl,
                        const double *Yin_row, const double *Min, double tau, double P, double Tspec, int energy,
                        const double *__restrict__ mult) {
@@ -204,13 +207,19 @@ __device__ PSR_STAGE void eval_F(const DevMech &M, const WS<TJ> &w, const V2 &y,
         if (j < K) {
             double Yj = h ? y.b : y.a;
             double cpR, hRT, sR, dcpR;
-            nasa7(M.nasa, j, T, lnT, invT, cpR, hRT, sR, dcpR);
             const double invW = __ldg(M.invW + j);
             w.C[j] = rho * Yj * invW;
-            w.hRT[j] = hRT;
-            w.gS[j] = sR - hRT;
-            sl.cpR[h] = cpR;
-            sl.dcpR[h] = dcpR;
+            if constexpr (FRZ) {
+                hRT = w.hRT[j];
+                cpR = sl.cpR[h];
+                dcpR = sl.dcpR[h];
+            } else {
+                nasa7(M.nasa, j, T, lnT, invT, cpR, hRT, sR, dcpR);
+                w.hRT[j] = hRT;
+                w.gS[j] = sR - hRT;
+                sl.cpR[h] = cpR;
+                sl.dcpR[h] = dcpR;
+            }
             const double yin = Yin_row[j];
             s_yin_h += yin * hRT * invW;
             s_cp += Yj * cpR * invW;
@@ -244,18 +253,33 @@ __device__ PSR_STAGE void eval_F(const DevMech &M, const WS<TJ> &w, const V2 &y,
                           __ldg(M.dnu_d + i1) * mx.lnPRT;
         const double Pf0 = w.C[a[0]] * w.C[a[1]] * w.C[a[2]], Pr0 = w.C[a[3]] * w.C[a[4]] * w.C[a[5]];
         const double Pf1 = w.C[b[0]] * w.C[b[1]] * w.C[b[2]], Pr1 = w.C[b[3]] * w.C[b[4]] * w.C[b[5]];
-        const double kf0 = exp(A0), kf1 = exp(A1), kr0 = exp(A0 - K0), kr1 = exp(A1 - K1);
+        double kf0, kf1, kr0, kr1;
+        if constexpr (FRZ) {
+            kf0 = w.kf[i0];
+            kf1 = w.kf[i1];
+            kr0 = w.kr[i0];
+            kr1 = w.kr[i1];
+        } else {
+            kf0 = exp(A0);
+            kf1 = exp(A1);
+            kr0 = exp(A0 - K0);
+            kr1 = exp(A1 - K1);
+        }
         double q0 = kf0 * Pf0 - kr0 * Pr0, q1 = kf1 * Pf1 - kr1 * Pr1;
         if (mult) {
             q0 *= __ldg(mult + __ldg(M.orig + i0));
             q1 *= __ldg(mult + __ldg(M.orig + i1));
         }
-        w.kf[i0] = kf0;
-        w.kr[i0] = kr0;
+        if constexpr (!FRZ) {
+            w.kf[i0] = kf0;
+            w.kr[i0] = kr0;
+        }
         w.q[i0] = q0;
         if (i1 != i0) {
-            w.kf[i1] = kf1;
-            w.kr[i1] = kr1;
+            if constexpr (!FRZ) {
+                w.kf[i1] = kf1;
+                w.kr[i1] = kr1;
+            }
             w.q[i1] = q1;
         }
     }
@@ -267,22 +291,33 @@ __device__ PSR_STAGE void eval_F(const DevMech &M, const WS<TJ> &w, const V2 &y,
         const double a = __ldg(M.lnA + i) + __ldg(M.beta + i) * lnT - __ldg(M.theta + i) * invT;
         const double lnKc = (w.gS[s3] + w.gS[s4] + w.gS[s5]) - (w.gS[s0] + w.gS[s1] + w.gS[s2]) +
                             __ldg(M.dnu_d + i) * mx.lnPRT;
-        double kf = exp(a), kr = exp(a - lnKc);
         const int typ = __ldg(M.type + i);
+        double kf, kr;
+        if (FRZ && typ == kThirdBody) {
+            kf = w.kf[i];
+            kr = w.kr[i];
+        } else {
+            kf = exp(a);
+            kr = exp(a - lnKc);
+        }
         double Mc = mx.Ctot;
         for (int e = __ldg(M.eff_ptr + i); e < __ldg(M.eff_ptr + i + 1); ++e)
             Mc += __ldg(M.eff_val + e) * w.C[__ldg(M.eff_sp + e)];
         if (typ == kTroe) {
             const int tr = __ldg(M.troe_row + i);
-            Troe t = troe_eval(M.troe + size_t(tr) * 8, a, Mc, T, lnT, invT, true);
+            Troe t = troe_eval(M.troe + size_t(tr) * 8, a, Mc, T, lnT, invT, !FRZ);
             kf *= t.fac;
             kr *= t.fac;
-            const double dlkf = __ldg(M.beta + i) * invT + __ldg(M.theta + i) * invT * invT;
-            w.tD[tr] = t.D;
-            w.tX[tr] = t.D * (t.dlk0 - dlkf) + t.dlnF_dT;
+            if constexpr (!FRZ) {
+                const double dlkf = __ldg(M.beta + i) * invT + __ldg(M.theta + i) * invT * invT;
+                w.tD[tr] = t.D;
+                w.tX[tr] = t.D * (t.dlk0 - dlkf) + t.dlnF_dT;
+            }
         }
-        w.kf[i] = kf;
-        w.kr[i] = kr;
+        if constexpr (!FRZ) {
+            w.kf[i] = kf;
+            w.kr[i] = kr;
+        }
         double q = kf * (w.C[s0] * w.C[s1] * w.C[s2]) - kr * (w.C[s3] * w.C[s4] * w.C[s5]);
         if (typ == kThirdBody) q *= Mc;
         if (mult) q *= __ldg(mult + __ldg(M.orig + i));
@@ -638,6 +673,52 @@ __device__ PSR_STAGE void eval_J(const DevMech &M, const WS<TJ> &w, const V2 &y,
     __syncwarp();
 }
 
+// ---------------------------------------------------------------- finite-difference Jacobian
+// The paper's Jacobian (Sec. 1): central differences of the residual, column j with
+// h_j = 1e-6 max(|x_j|, s_j), s = 0.1 for mass fractions and 1000 K for T. The mass-
+// fraction columns use the frozen-rate residual (the rate constants depend on T only,
+// Sec. 3), so only the temperature column re-evaluates the exponentials; it comes last,
+// after the base state's caches have served every other column. Gas mechanisms only.
+template <class TJ>
+__device__ void eval_J_fd(const DevMech &M, const WS<TJ> &w, const V2 &y, const V2 &c, Mix &mx, SpecLane &sl,
+                          const double *Yin_row, double tau, double P, double Tspec, int energy,
+                          const double *__restrict__ mult) {
+    const int lane = threadIdx.x & 31;
+    const int K = M.K, n = K + 1, Pp = w.P;
+    V2 F0, Fp, Fm;
+    eval_F<TJ, false, false>(M, w, y, F0, mx, sl, Yin_row, nullptr, tau, P, Tspec, energy, mult);
+    for (int j = 0; j < n; ++j) {
+        const double xj = comp_get(y, j);
+        const double h = 1e-6 * fmax(fabs(xj), j < K ? 0.1 : 1000.0);
+        V2 yp = y, ym = y;
+        if (lane == (j & 31)) {
+            if (j < 32) {
+                yp.a += h;
+                ym.a -= h;
+            } else {
+                yp.b += h;
+                ym.b -= h;
+            }
+        }
+        if (j < K) {
+            eval_F<TJ, false, true>(M, w, yp, Fp, mx, sl, Yin_row, nullptr, tau, P, Tspec, energy, mult);
+            eval_F<TJ, false, true>(M, w, ym, Fm, mx, sl, Yin_row, nullptr, tau, P, Tspec, energy, mult);
+        } else {
+            eval_F<TJ, false, false>(M, w, yp, Fp, mx, sl, Yin_row, nullptr, tau, P, Tspec, energy, mult);
+            eval_F<TJ, false, false>(M, w, ym, Fm, mx, sl, Yin_row, nullptr, tau, P, Tspec, energy, mult);
+        }
+        const double inv2h = 0.5 / h;
+        if (lane < n) w.J[size_t(lane) * Pp + j] = TJ((Fp.a - Fm.a) * inv2h);
+        if (lane + 32 < n) w.J[size_t(lane + 32) * Pp + j] = TJ((Fp.b - Fm.b) * inv2h);
+    }
+    __syncwarp();
+    for (int h = 0; h < 2; ++h) {
+        const int j = lane + 32 * h;
+        if (j < n) w.J[size_t(j) * Pp + j] = TJ(double(w.J[size_t(j) * Pp + j]) + (h ? c.b : c.a));
+    }
+    __syncwarp();
+}
+
 // ---------------------------------------------------------------- LU (partial pivoting)
 // In-place LU of w.J (n x n) with row interchanges; perm holds the final row order.
 // Returns false on a zero or non-finite pivot.
@@ -867,18 +948,23 @@ __device__ void residual_R(Ctx &cx, const WS<TJ> &w, const V2 &y, const V2 &c, c
 }
 
 // Damped Newton on R(y) = F(y) + c (y - xref) from y (see the oracle's description).
-template <class TJ, bool SOOT>
+template <class TJ, bool SOOT, bool FDJ = false>
 __device__ bool damped_newton(Ctx &cx, const WS<TJ> &w, V2 &y, const V2 &xref, const V2 &c, int max_it,
-                              bool steady, int &counter) {
+                              bool steady, int &counter, double *fnorm) {
     const int K = cx.K, n = cx.n;
     const Opts &o = cx.o;
     V2 F, R;
     residual_R<TJ, SOOT>(cx, w, y, c, xref, F, R);
+    // ||F||_inf of the steady residual at the first and the last evaluated point
+    if (fnorm) fnorm[0] = fnorm[1] = wmax(fmax(fabs(F.a), fabs(F.b)));
     double dn_prev = INFINITY;
     for (int it = 0; it < max_it; ++it) {
         if (counter >= o.max_newton) break;
         ++counter;
-        eval_J<TJ, SOOT>(cx.M, w, y, c, cx.mx, cx.sl, cx.r.Yin, cx.r.Min, cx.r.tau, o.energy, cx.mult);
+        if constexpr (FDJ)
+            eval_J_fd<TJ>(cx.M, w, y, c, cx.mx, cx.sl, cx.r.Yin, cx.r.tau, cx.r.P, cx.r.Tspec, o.energy, cx.mult);
+        else
+            eval_J<TJ, SOOT>(cx.M, w, y, c, cx.mx, cx.sl, cx.r.Yin, cx.r.Min, cx.r.tau, o.energy, cx.mult);
         if (!lu_factor(w, n)) break;
         V2 dy;
         lu_solve_neg(w, n, R, dy);
@@ -904,6 +990,7 @@ __device__ bool damped_newton(Ctx &cx, const WS<TJ> &w, V2 &y, const V2 &xref, c
             if (in_bounds(yt, K, o)) {
                 V2 Ft;
                 residual_R<TJ, SOOT>(cx, w, yt, c, xref, Ft, Rt);
+                if (fnorm) fnorm[1] = wmax(fmax(fabs(Ft.a), fabs(Ft.b)));
                 if (all_finite(Rt)) {
                     V2 db;
                     lu_solve_neg(w, n, Rt, db);
@@ -964,7 +1051,7 @@ __device__ void init_moments(Ctx &cx, const Batch &bt, int64_t r, V2 &x) {
     }
 }
 
-template <class TJ, bool SOOT>
+template <class TJ, bool SOOT, bool FDJ = false>
 __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) {
     const int lane = threadIdx.x & 31;
     const int K = cx.K;
@@ -1006,7 +1093,8 @@ __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) 
         double dt = o.dt0_over_tau * tau;
         while (true) {
             V2 y = x;
-            bool conv = damped_newton<TJ, SOOT>(cx, w, y, x, zero, o.max_newton, true, counter);
+            double fn[2];
+            bool conv = damped_newton<TJ, SOOT, FDJ>(cx, w, y, x, zero, o.max_newton, true, counter, fn);
             if (conv) {
                 status = PSR_CONVERGED;
                 out = y;
@@ -1025,6 +1113,7 @@ __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) 
             }
             int taken = 0;
             bool done = false;
+            double f_prev = fn[0];   // ||F(x)||_inf of the estimate being conditioned
             while (taken < o.ts_steps) {
                 const double Tx = comp_get(x, K);
                 const double s = tau / dt;
@@ -1034,7 +1123,8 @@ __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) 
                 c.b = (lane + 32 < K) ? s : (lane + 32 == K ? sT : (lane + 32 < cx.n ? s : 0.0));
                 const int used0 = counter;
                 V2 y = x;
-                bool ok = damped_newton<TJ, SOOT>(cx, w, y, x, c, o.ts_newton, false, counter);
+                double fs[2];
+                bool ok = damped_newton<TJ, SOOT, FDJ>(cx, w, y, x, c, o.ts_newton, false, counter, fs);
                 const int used = counter - used0;
                 if (counter >= o.max_newton) {
                     status = PSR_MAX_ITER;
@@ -1046,7 +1136,11 @@ __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) 
                     x = y;
                     ++taken;
                     ++ts;
-                    const double g = (used <= 3) ? 2.0 : (used == 4 ? 1.25 : 1.0);
+                    // growth by how easily the step was solved, times its reduction of ||F||
+                    // clipped to [1, 4] (switched evolution relaxation)
+                    double g = (used <= 3) ? 2.0 : (used == 4 ? 1.25 : 1.0);
+                    if (fs[1] > 0.0) g *= fmin(4.0, fmax(1.0, f_prev / fs[1]));
+                    f_prev = fs[1];
                     dt = fmin(g * dt, 1e6 * tau);
                 } else {
                     dt *= o.dt_shrink;
@@ -1092,7 +1186,7 @@ __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) 
 #endif
 constexpr int kMaxSolveWarps = 4;   // the solver kernel's block holds at most 4 warps (128 threads)
 constexpr int kDefaultSolveWarps = 2;   // measured best at K = 53 for both forms (finer shared-memory packing)
-template <class TJ, bool SOOT>
+template <class TJ, bool SOOT, bool FDJ = false>
 __global__ void __launch_bounds__(128, PSR_MIN_BLOCKS) solve_kernel(DevMech M, Batch bt, Opts o, int *queue,
                                                                    size_t ws_per_warp) {
     extern __shared__ __align__(16) char smem[];
@@ -1112,7 +1206,7 @@ __global__ void __launch_bounds__(128, PSR_MIN_BLOCKS) solve_kernel(DevMech M, B
         p = __shfl_sync(kFull, p, 0);
         if (p >= nwork) break;
         const int64_t r = bt.list ? int64_t(bt.list[p]) : int64_t(p);
-        solve_one<TJ, SOOT>(cx, w, bt, r);
+        solve_one<TJ, SOOT, FDJ>(cx, w, bt, r);
     }
 }
 
@@ -1178,6 +1272,14 @@ __global__ void eval_kernel(DevMech M, Batch bt, int energy, int want_J, double 
         }
         if (ro.wdot)
             for (int j = lane; j < K; j += 32) ro.wdot[r * K + j] = w.v[j];
+        return;
+    }
+    if (want_J == 3) {   // finite-difference Jacobian (gas mechanisms)
+        if constexpr (!SOOT) {
+            eval_J_fd<TJ>(M, w, y, zero, cx.mx, cx.sl, cx.r.Yin, cx.r.tau, cx.r.P, cx.r.Tspec, energy, cx.mult);
+            for (int idx = lane; idx < n * n; idx += 32)
+                out[r * n * n + idx] = double(w.J[size_t(idx / n) * w.P + idx % n]);
+        }
         return;
     }
     if (!want_J) {
@@ -1315,6 +1417,7 @@ Opts to_opts(const psr_options *po) {
     o.max_ts_rounds = s.max_ts_rounds;
     o.ts_steps = s.ts_steps;
     o.ts_newton = s.ts_newton;
+    o.jac_fd = s.jacobian;
     o.energy = s.energy;
     return o;
 }
@@ -1328,12 +1431,13 @@ int check_opts(const psr_options *po) {
         s.max_ts_rounds < 0 || s.ts_steps < 1 || s.ts_newton < 1 ||
         (s.precision != PSR_FP64 && s.precision != PSR_MIXED) ||
         (s.energy != PSR_ADIABATIC && s.energy != PSR_FIXED_T) || s.warps_per_block < 0 || s.warps_per_block > 32 ||
-        s.blocks_per_sm < 0 || (s.mixed_fallback != 0 && s.mixed_fallback != 1))
+        s.blocks_per_sm < 0 || (s.mixed_fallback != 0 && s.mixed_fallback != 1) ||
+        (s.jacobian != PSR_JAC_ANALYTIC && s.jacobian != PSR_JAC_FD))
         return set_error(PSR_E_ARG, "psr_options: value out of range");
     return PSR_OK;
 }
 
-template <class TJ, bool SOOT>
+template <class TJ, bool SOOT, bool FDJ = false>
 int launch_solve_qs(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int bps_req, cudaStream_t st,
                     int *queue) {
     const size_t wsb = ws_bytes<TJ>(m.K, m.I, m.K + 1 + m.dev.nsoot, m.n_troe, m.dev.nsoot);
@@ -1347,11 +1451,11 @@ int launch_solve_qs(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, 
     const size_t smem = size_t(wpb) * wsb;
     if (smem > size_t(max_smem))
         return set_error(PSR_E_UNSUPPORTED, "mechanism too large for one warp's shared memory");
-    cudaError_t e = cudaFuncSetAttribute(solve_kernel<TJ, SOOT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(solve_kernel<TJ, SOOT, FDJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(smem));
     if (e != cudaSuccess) return cuda_error("cudaFuncSetAttribute", e);
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel<TJ, SOOT>, wpb * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel<TJ, SOOT, FDJ>, wpb * 32, smem);
     if (e != cudaSuccess) return cuda_error("occupancy", e);
     if (per_sm < 1) return set_error(PSR_E_UNSUPPORTED, "solver kernel does not fit on an SM");
     if (bps_req > 0 && bps_req < per_sm) per_sm = bps_req;
@@ -1360,7 +1464,7 @@ int launch_solve_qs(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, 
     if (grid < 1) grid = 1;
     e = cudaMemsetAsync(queue, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_error("cudaMemsetAsync(work queue)", e);
-    solve_kernel<TJ, SOOT><<<unsigned(grid), wpb * 32, smem, st>>>(m.dev, bt, o, queue, wsb);
+    solve_kernel<TJ, SOOT, FDJ><<<unsigned(grid), wpb * 32, smem, st>>>(m.dev, bt, o, queue, wsb);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error("solve_kernel launch", e);
     return PSR_OK;
@@ -1372,6 +1476,7 @@ template <class TJ>
 int launch_solve_q(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int bps_req, cudaStream_t st,
                    int *queue) {
     if (m.dev.nsoot) return launch_solve_qs<TJ, true>(m, bt, o, wpb_req, bps_req, st, queue);
+    if (o.jac_fd) return launch_solve_qs<TJ, false, true>(m, bt, o, wpb_req, bps_req, st, queue);
     return launch_solve_qs<TJ, false>(m, bt, o, wpb_req, bps_req, st, queue);
 }
 
@@ -1597,6 +1702,8 @@ int psr_batch_solve(const psr_mech *m, int64_t B, const double *Y_in, const doub
     psr_options_default(&d);
     const psr_options &po = opt ? *opt : d;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (po.jacobian == PSR_JAC_FD && !warp_path(m))
+        return set_error(PSR_E_UNSUPPORTED, "finite-difference Jacobian: K + 1 <= 64 only");
     if (!warp_path(m))
         return block_solve(m->m, bt, o, po.precision, po.mixed_fallback != 0, po.blocks_per_sm, st);
     if (po.precision == PSR_MIXED)
@@ -1990,6 +2097,20 @@ int psr_eval_rates(const psr_mech *m, int64_t B, const double *Y, const double *
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (!warp_path(m)) return block_eval(m->m, bt, PSR_FIXED_T, 2, PSR_FP64, nullptr, st, ro);
     return launch_eval<double>(m->m, bt, PSR_FIXED_T, 2, nullptr, st, ro);
+}
+
+int psr_eval_jacobian_fd(const psr_mech *m, int64_t B, const double *Y_in, const double *T_in, const double *tau,
+                         const double *P, const double *Y, const double *T, const double *rate_mult, double *J_out,
+                         int32_t energy, void *cuda_stream) {
+    int rc = check_mech(m);
+    if (rc) return rc;
+    if (m->m.has_soot || !warp_path(m))
+        return set_error(PSR_E_UNSUPPORTED, "finite-difference Jacobian: gas mechanisms with K + 1 <= 64");
+    if (B < 0 || (energy != PSR_ADIABATIC && energy != PSR_FIXED_T)) return set_error(PSR_E_ARG, "bad B or energy");
+    if (B == 0) return PSR_OK;
+    if (!Y_in || !T_in || !tau || !P || !Y || !T || !J_out) return set_error(PSR_E_ARG, "NULL pointer");
+    Batch bt{B, Y_in, T_in, tau, P, Y, T, rate_mult, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    return launch_eval<double>(m->m, bt, energy, 3, J_out, static_cast<cudaStream_t>(cuda_stream));
 }
 
 }  // extern "C"

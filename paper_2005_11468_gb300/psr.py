@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libpsr.so")
 PSR_OK = 0
 PSR_CONVERGED, PSR_MAX_ITER, PSR_NONFINITE, PSR_TS_EXHAUSTED, PSR_REFINE_FALLBACK = 0, 1, 2, 4, 5
 PSR_BAD_INPUT = 7
+PSR_JAC_ANALYTIC, PSR_JAC_FD = 0, 1
 CONVERGED_STATES = (PSR_CONVERGED, PSR_REFINE_FALLBACK)
 PSR_FP64, PSR_MIXED = 0, 1
 PSR_ADIABATIC, PSR_FIXED_T = 0, 1
@@ -46,7 +47,7 @@ class COptions(ctypes.Structure):
                 ("ts_newton", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("energy", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("mixed_fallback", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("jacobian", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 _lib = None
@@ -80,6 +81,7 @@ def lib():
         L.psr_batch_solve_soot.argtypes = [vp, i64] + [dp] * 9 + [dp] * 3 + [dp] * 5 + [ctypes.POINTER(COptions), vp]
         L.psr_eval_residual_soot.argtypes = [vp, i64] + [dp] * 9 + [dp, i32, vp]
         L.psr_eval_jacobian_soot.argtypes = [vp, i64] + [dp] * 9 + [dp, i32, i32, vp]
+        L.psr_eval_jacobian_fd.argtypes = [vp, i64] + [dp] * 7 + [dp, i32, vp]
         L.psr_eval_rates.argtypes = [vp, i64] + [dp] * 8 + [vp]
         L.psr_autotune.argtypes = [vp, i64] + [dp] * 6 + [ctypes.POINTER(COptions), vp]
         L.psr_batch_solve_multi.argtypes = [ctypes.POINTER(vp), i32, i64, dp, dp] + [dp] * 8 + [dp] * 5 + \
@@ -117,6 +119,7 @@ class Options:
     warps_per_block: int = 0
     blocks_per_sm: int = 0
     mixed_fallback: int = 1
+    jacobian: int = 0
 
     def to_c(self):
         o = COptions()
@@ -283,6 +286,19 @@ def eval_jacobian(mech: Mechanism, Y_in, T_in, tau, P, Y, T, rate_mult=None, ene
         mech.handle, B, _ptr(Y_in, f64, (B, K)), _ptr(T_in, f64, (B,)), _ptr(tau, f64, (B,)),
         _ptr(P, f64, (B,)), _ptr(Y, f64, (B, K)), _ptr(T, f64, (B,)), _ptr(rate_mult, f64, (mech.I,)),
         J.data_ptr(), energy, precision, _stream()))
+    return J
+
+
+def eval_jacobian_fd(mech: Mechanism, Y_in, T_in, tau, P, Y, T, rate_mult=None, energy=PSR_ADIABATIC):
+    """psr_eval_jacobian_fd: the central-difference Jacobian [B][K+1][K+1] (FP64)."""
+    import torch
+    f64 = torch.float64
+    B, K = Y.shape
+    J = torch.empty((B, K + 1, K + 1), dtype=f64, device=Y.device)
+    _check(lib().psr_eval_jacobian_fd(
+        mech.handle, B, _ptr(Y_in, f64, (B, K)), _ptr(T_in, f64, (B,)), _ptr(tau, f64, (B,)),
+        _ptr(P, f64, (B,)), _ptr(Y, f64, (B, K)), _ptr(T, f64, (B,)), _ptr(rate_mult, f64, (mech.I,)),
+        J.data_ptr(), energy, _stream()))
     return J
 
 

@@ -352,3 +352,45 @@ def test_fixed_t_sweep_with_continuation(dev):
         assert r.status == O.CONVERGED
         big = r.x[:-1] > Y_MIN
         assert np.max(np.abs(Yc[a, j][big] - r.x[:-1][big]) / r.x[:-1][big]) <= Y_REL
+
+
+@pytest.mark.parametrize("name", ["k10_b64", "k53_b4096"])
+def test_fd_jacobian_matches_oracle_differences(dev, name):
+    """psr_eval_jacobian_fd (the paper's finite-difference Jacobian; mass-fraction columns
+    with frozen rate constants) against the oracle's central differences with the same
+    steps, and against the analytic Jacobian to the differences' truncation level."""
+    import torch
+    _, mech, batch = workload(name)
+    m = 6
+    X = random_states(mech, m, seed=41)
+    sub = batch.subset(range(m))
+    t = to_dev(sub, dev)
+    Yd = torch.tensor(X[:, :-1], device=dev)
+    Td = torch.tensor(X[:, -1], device=dev)
+    Jf = psr.eval_jacobian_fd(gpu_mech(name), t["Y_in"], t["T_in"], t["tau"], t["P"], Yd, Td).cpu().numpy()
+    Ja = psr.eval_jacobian(gpu_mech(name), t["Y_in"], t["T_in"], t["tau"], t["P"], Yd, Td).cpu().numpy()
+    for b in range(m):
+        S = O.GasSystem(mech, O.inlet_of(sub, b))
+        Jo = O.jacobian_fd(S, X[b], O.Options())
+        rowmax = np.max(np.abs(Jo), axis=1, keepdims=True)
+        assert np.max(np.abs(Jf[b] - Jo) / rowmax) <= 1e-6
+        assert np.max(np.abs(Jf[b] - Ja[b]) / np.max(np.abs(Ja[b]), axis=1, keepdims=True)) <= 1e-3
+
+
+def test_fd_jacobian_solves_reach_the_same_roots(dev):
+    """Newton with the finite-difference Jacobian converges to the analytic-Jacobian roots."""
+    _, mech, batch = workload("k10_b64")
+    t = to_dev(batch, dev)
+    gm = gpu_mech("k10_b64")
+    a = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"])
+    f = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"],
+                        opts=psr.Options(jacobian=psr.PSR_JAC_FD))
+    sa, sf = a["status"].cpu().numpy(), f["status"].cpu().numpy()
+    both = (sa == 0) & (sf == 0) & (np.abs(a["T"].cpu().numpy() - f["T"].cpu().numpy()) < 1.0)
+    assert both.mean() >= 0.8
+    Ya, Yf = a["Y"].cpu().numpy()[both], f["Y"].cpu().numpy()[both]
+    big = Ya > Y_MIN
+    assert np.max(np.where(big, np.abs(Yf - Ya) / np.where(big, Ya, 1.0), 0.0)) <= Y_REL
+    assert np.all(f["fnorm"].cpu().numpy()[sf == 0] <= 1e-8)
+    with pytest.raises(psr.PsrError):
+        psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"], opts=psr.Options(jacobian=7))
