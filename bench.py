@@ -37,6 +37,9 @@ FP64_PEAK_TFLOPS = 1.25          # nominal GB300 FP64 (non-tensor) rate
 # FP64-pipe cost of one transcendental in flop slots (measured GB300 throughput of CUDA's
 # double exp / log relative to the FP64 FMA rate: 1.2 TFLOP/s / 29.6 G exp/s, / 16.3 G log/s)
 EXP_FLOPS, LOG_FLOPS, DIV_FLOPS = 40.0, 73.0, 16.0
+# dram__bytes_read + write of one mixed-form launch on k53_b4096, from the ncu capture of
+# the current solver build (to be re-measured whenever the kernel changes)
+K53_TRAFFIC_BYTES = 4336896
 
 
 def parse():
@@ -366,7 +369,9 @@ def run_ours(args):
         "converged_fraction": mixed["conv"] / B,
         "newton_iters_median": float(np.median(mixed["iters"])),
         "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": K53_TRAFFIC_BYTES if args.workload == WORKLOAD else None,
+                     "traffic_unit": "DRAM bytes per mixed launch (ncu capture, profiles/solve_kernel_k53_b4096.md)",
                      "peak_source": "nominal GB300 FP64 rate (recipe table); measured FMA loop 1.198",
                      "work_model": "FP64 flops with exp=40, log=73, div=16 flop slots"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
