@@ -1292,6 +1292,78 @@ __global__ void eval_kernel(DevMech M, Batch bt, int energy, int want_J, double 
         out[r * n * n + idx] = double(w.J[size_t(idx / n) * w.P + idx % n]);
 }
 
+// Rates at given states, one warp per state (any K): NASA-7 Gibbs terms and
+// concentrations per species, then per reaction k_f (Eq. (6)), K_c (Eqs. (8)-(9)),
+// k_r (Eq. (7)), the third-body and falloff forms and q (Eq. (5)), written in the
+// mechanism file's order; wdot (Eq. (4)) gathered per species from q kept in shared
+// memory. Per warp: C and S/R - H/RT [K+1], q [I] (doubles).
+__global__ void rates_kernel(DevMech M, int64_t B, const double *Y, const double *Tv, const double *Pv,
+                             const double *__restrict__ mult, RatesOut ro) {
+    extern __shared__ __align__(16) char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    const int K = M.K, I = M.I;
+    double *C = reinterpret_cast<double *>(smem) + size_t(warp) * (2 * (K + 1) + I);
+    double *gS = C + (K + 1), *q = gS + (K + 1);
+    for (int64_t r = int64_t(blockIdx.x) * wpb + warp; r < B; r += int64_t(gridDim.x) * wpb) {
+        const double T = Tv[r], P = Pv[r];
+        const double lnT = log(T), invT = 1.0 / T;
+        const double *Yr = Y + r * K;
+        double sYW = 0.0;
+        for (int k = lane; k < K; k += 32) sYW += Yr[k] * __ldg(M.invW + k);
+        sYW = wsum(sYW);
+        const double rho = P / (sYW * kRu * T), Ctot = P / (kRu * T), lnPRT = log(kPatm / (kRu * T));
+        for (int k = lane; k < K; k += 32) {
+            double cpR, hRT, sR, dcpR;
+            nasa7(M.nasa, k, T, lnT, invT, cpR, hRT, sR, dcpR);
+            C[k] = rho * Yr[k] * __ldg(M.invW + k);
+            gS[k] = sR - hRT;
+        }
+        if (lane == 0) {
+            C[K] = 1.0;
+            gS[K] = 0.0;
+        }
+        __syncwarp();
+        for (int i = lane; i < I; i += 32) {
+            const int16_t *sl6 = M.slots + size_t(i) * 6;
+            const int s0 = __ldg(sl6), s1 = __ldg(sl6 + 1), s2 = __ldg(sl6 + 2), s3 = __ldg(sl6 + 3),
+                      s4 = __ldg(sl6 + 4), s5 = __ldg(sl6 + 5);
+            const double a = __ldg(M.lnA + i) + __ldg(M.beta + i) * lnT - __ldg(M.theta + i) * invT;
+            const double lnKc = (gS[s3] + gS[s4] + gS[s5]) - (gS[s0] + gS[s1] + gS[s2]) + __ldg(M.dnu_d + i) * lnPRT;
+            double kf = exp(a), kr = exp(a - lnKc);
+            const int typ = __ldg(M.type + i);
+            double Mc = 1.0;
+            if (typ != kElem) {
+                Mc = Ctot;
+                for (int e = __ldg(M.eff_ptr + i); e < __ldg(M.eff_ptr + i + 1); ++e)
+                    Mc += __ldg(M.eff_val + e) * C[__ldg(M.eff_sp + e)];
+                if (typ == kTroe) {
+                    const Troe t = troe_eval(M.troe + size_t(__ldg(M.troe_row + i)) * 8, a, Mc, T, lnT, invT, false);
+                    kf *= t.fac;
+                    kr *= t.fac;
+                }
+            }
+            double qi = kf * (C[s0] * C[s1] * C[s2]) - kr * (C[s3] * C[s4] * C[s5]);
+            if (typ == kThirdBody) qi *= Mc;
+            if (mult) qi *= __ldg(mult + __ldg(M.orig + i));
+            q[i] = qi;
+            const int64_t o = r * I + __ldg(M.orig + i);
+            if (ro.kf) ro.kf[o] = kf;
+            if (ro.kr) ro.kr[o] = kr;
+            if (ro.q) ro.q[o] = qi;
+        }
+        __syncwarp();
+        if (ro.wdot) {
+            for (int k = lane; k < K; k += 32) {
+                double wd = 0.0;
+                for (int e = __ldg(M.sp_ptr + k); e < __ldg(M.sp_ptr + k + 1); ++e)
+                    wd += __ldg(M.sp_nu_d + e) * q[__ldg(M.sp_rxn + e)];
+                ro.wdot[r * K + k] = wd;
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // Adjoint sensitivities at given (converged) states, one warp per reactor: FP64
 // Jacobian, transposed LU solve J^T lam = g, then per reaction
 // dL/d ln m_i = -lam . dF/d ln m_i = (tau q_i / rho) [sum_k lam_k W_k nu_ki - lam_T dH_i / (c_p T)].
@@ -2091,12 +2163,28 @@ int psr_eval_rates(const psr_mech *m, int64_t B, const double *Y, const double *
     if (B < 0) return set_error(PSR_E_ARG, "B < 0");
     if (B == 0) return PSR_OK;
     if (!Y || !T || !P) return set_error(PSR_E_ARG, "psr_eval_rates: NULL state pointer");
-    // the residual machinery runs with the state as its own inlet (the residual is discarded)
-    Batch bt{B, Y, T, P, P, Y, T, rate_mult, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     RatesOut ro{kf_out, kr_out, q_out, wdot_out};
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    if (!warp_path(m)) return block_eval(m->m, bt, PSR_FIXED_T, 2, PSR_FP64, nullptr, st, ro);
-    return launch_eval<double>(m->m, bt, PSR_FIXED_T, 2, nullptr, st, ro);
+    const Mech &mm = m->m;
+    const size_t per_warp = sizeof(double) * (2 * size_t(mm.K + 1) + size_t(mm.I));
+    int dev = 0, max_smem = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int wpb = 8;
+    while (wpb > 1 && size_t(wpb) * per_warp > size_t(max_smem)) --wpb;
+    const size_t smem = size_t(wpb) * per_warp;
+    if (smem > size_t(max_smem)) return set_error(PSR_E_UNSUPPORTED, "psr_eval_rates: mechanism too large");
+    cudaError_t e = cudaFuncSetAttribute(rates_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return cuda_error("cudaFuncSetAttribute", e);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rates_kernel, wpb * 32, smem);
+    if (e != cudaSuccess) return cuda_error("occupancy", e);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(int64_t(std::max(per_sm, 1)) * nsm, (B + wpb - 1) / wpb));
+    rates_kernel<<<unsigned(grid), wpb * 32, smem, st>>>(mm.dev, B, Y, T, P, rate_mult, ro);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error("rates_kernel launch", e);
+    return PSR_OK;
 }
 
 int psr_eval_jacobian_fd(const psr_mech *m, int64_t B, const double *Y_in, const double *T_in, const double *tau,
