@@ -174,3 +174,28 @@ def test_k200_adjoint(env):
         assert np.all(np.abs(grad[j] - go) <= bound), (j, np.max(np.abs(grad[j] - go) - bound))
         checked += 1
     assert checked >= 1
+
+
+@pytest.mark.parametrize("K", [63, 64])
+def test_warp_block_boundary(env, K):
+    """K + 1 = 64 is the largest system of the warp-per-reactor path and K + 1 = 65 the
+    smallest of the block-per-reactor path: both solve to the oracle's roots."""
+    import torch
+    spec = synth.make_mechanism(K, 4 * K, n_tb=4, n_troe=4, seed=synth.MECH_SEED_BASE + 700 + K)
+    text = synth.mechanism_text(spec)
+    mech, gm = O.Mechanism(text), psr.Mechanism(text)
+    batch = synth.make_batch(spec, 8, seed=synth.MECH_SEED_BASE + 701 + K)
+    t = _t(env, batch)
+    for prec in (psr.PSR_FP64, psr.PSR_MIXED):
+        out = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"],
+                              opts=psr.Options(precision=prec))
+        st, Y, T = out["status"].cpu().numpy(), out["Y"].cpu().numpy(), out["T"].cpu().numpy()
+        assert np.isin(st, psr.CONVERGED_STATES).mean() >= 0.75
+        for b in (0, 1):
+            r = O.solve_reactor(mech, O.inlet_of(batch, b), np.r_[batch.Y0[b], batch.T0[b]])
+            if r.status != O.CONVERGED or abs(T[b] - r.x[-1]) > 1.0:
+                continue
+            assert st[b] in psr.CONVERGED_STATES
+            big = r.x[:-1] > Y_MIN
+            assert np.max(np.abs(Y[b][big] - r.x[:-1][big]) / r.x[:-1][big]) <= Y_REL
+            assert abs(T[b] - r.x[-1]) <= T_ABS
