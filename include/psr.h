@@ -107,7 +107,10 @@ typedef struct {
     int32_t mixed_fallback; /* 1 (default): PSR_MIXED re-solves unconverged reactors in FP64 */
     int32_t jacobian;       /* PSR_JAC_ANALYTIC (default) or PSR_JAC_FD: central differences
                                as the paper builds it (Sec. 1), K + 1 <= 64 gas mechanisms */
-    int32_t reserved[5];
+    int32_t mixed_max_newton; /* 300: Newton cap of the FP32-Jacobian launch when the FP64
+                               re-solve follows (0 = max_newton); reactors it leaves are
+                               re-solved in FP64 with max_newton */
+    int32_t reserved[4];
 } psr_options;
 
 void psr_options_default(psr_options *o);

@@ -537,6 +537,7 @@ void psr_options_default(psr_options *o) {
     o->energy = PSR_ADIABATIC;
     o->mixed_fallback = 1;
     o->jacobian = PSR_JAC_ANALYTIC;
+    o->mixed_max_newton = 300;
 }
 
 }  // extern "C"

@@ -1192,7 +1192,9 @@ int block_solve(const Mech &m, const Batch &bt, const Opts &o, int precision, bo
         int32_t *len = scr + 2, *list = scr + 4;
         Batch b1 = bt;
         if (!bt.status) b1.status = scr + 4 + B;
-        rc = launch_block<float>(m, b1, o, bps_req, st, scr);
+        Opts first = o;   // the FP32 launch stops at the mixed_max_newton cap (see the warp solver)
+        if (o.mixed_max_newton > 0 && o.mixed_max_newton < o.max_newton) first.max_newton = o.mixed_max_newton;
+        rc = launch_block<float>(m, b1, first, bps_req, st, scr);
         if (rc == PSR_OK) {
             cudaMemsetAsync(len, 0, sizeof(int32_t), st);
             block_collect_unconverged<<<unsigned((B + 255) / 256), 256, 0, st>>>(bt.B, bt.list, bt.list_len,

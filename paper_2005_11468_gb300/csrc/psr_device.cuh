@@ -88,6 +88,7 @@ struct Opts {
         y_floor, t_min, t_max;
     int max_newton, max_damp, max_ts_rounds, ts_steps, ts_newton, energy;
     int jac_fd;   // Jacobian by central differences (the paper's method) instead of analytic
+    int mixed_max_newton;   // Newton cap of the FP32-Jacobian launch when the FP64 re-solve follows
 };
 
 // Scalars of the last residual evaluation that the Jacobian reuses.

@@ -1490,6 +1490,7 @@ Opts to_opts(const psr_options *po) {
     o.ts_steps = s.ts_steps;
     o.ts_newton = s.ts_newton;
     o.jac_fd = s.jacobian;
+    o.mixed_max_newton = s.mixed_max_newton;
     o.energy = s.energy;
     return o;
 }
@@ -1504,7 +1505,7 @@ int check_opts(const psr_options *po) {
         (s.precision != PSR_FP64 && s.precision != PSR_MIXED) ||
         (s.energy != PSR_ADIABATIC && s.energy != PSR_FIXED_T) || s.warps_per_block < 0 || s.warps_per_block > 32 ||
         s.blocks_per_sm < 0 || (s.mixed_fallback != 0 && s.mixed_fallback != 1) ||
-        (s.jacobian != PSR_JAC_ANALYTIC && s.jacobian != PSR_JAC_FD))
+        (s.jacobian != PSR_JAC_ANALYTIC && s.jacobian != PSR_JAC_FD) || s.mixed_max_newton < 0)
         return set_error(PSR_E_ARG, "psr_options: value out of range");
     return PSR_OK;
 }
@@ -1562,6 +1563,14 @@ int launch_solve(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int
     return rc;
 }
 
+// The FP32-Jacobian launch of the mixed form with fallback stops a reactor at the
+// mixed_max_newton cap, so reactors it would not converge reach the FP64 re-solve sooner.
+Opts mixed_first(const Opts &o) {
+    Opts f = o;
+    if (o.mixed_max_newton > 0 && o.mixed_max_newton < o.max_newton) f.max_newton = o.mixed_max_newton;
+    return f;
+}
+
 // Mixed form with per-reactor FP64 fallback: the FP32-Jacobian launch, then the reactors
 // it left unconverged (a device-side list, no host synchronisation) solved again from
 // their initial guesses with the FP64 Jacobian; those that converge get
@@ -1577,7 +1586,7 @@ int launch_mixed(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int
     int32_t *q0 = scr, *q1 = scr + 1, *len = scr + 2, *list = scr + 4;
     Batch b1 = bt;
     if (!bt.status) b1.status = scr + 4 + B;
-    int rc = launch_solve_q<float>(m, b1, o, wpb_req, bps_req, st, q0);
+    int rc = launch_solve_q<float>(m, b1, mixed_first(o), wpb_req, bps_req, st, q0);
     if (rc == PSR_OK) {
         cudaMemsetAsync(len, 0, sizeof(int32_t), st);
         collect_unconverged<<<unsigned((B + 255) / 256), 256, 0, st>>>(bt.B, bt.list, bt.list_len, b1.status, list,

@@ -47,7 +47,8 @@ class COptions(ctypes.Structure):
                 ("ts_newton", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("energy", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("mixed_fallback", ctypes.c_int32),
-                ("jacobian", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("jacobian", ctypes.c_int32), ("mixed_max_newton", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 _lib = None
@@ -120,6 +121,7 @@ class Options:
     blocks_per_sm: int = 0
     mixed_fallback: int = 1
     jacobian: int = 0
+    mixed_max_newton: int = 300
 
     def to_c(self):
         o = COptions()

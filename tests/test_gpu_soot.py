@@ -123,7 +123,10 @@ def test_mixed_fallback_resolves_in_fp64(env):
     batch = env["batch"].subset(range(2048))
     t = _t(env, batch)
     args = (env["gm"], t["Y_in"], t["T_in"], t["tau"], t["P"], t["M_in"], t["Y0"], t["T0"])
-    one = psr.batch_solve_soot(*args, opts=psr.Options(precision=psr.PSR_MIXED, mixed_fallback=0))
+    # the fallback's first launch stops at mixed_max_newton; the same cap without fallback
+    # is that launch on its own
+    cap = psr.Options().mixed_max_newton
+    one = psr.batch_solve_soot(*args, opts=psr.Options(precision=psr.PSR_MIXED, mixed_fallback=0, max_newton=cap))
     fb = psr.batch_solve_soot(*args, opts=psr.Options(precision=psr.PSR_MIXED, mixed_fallback=1))
     f64 = psr.batch_solve_soot(*args, opts=psr.Options(precision=psr.PSR_FP64))
     s1, sf, s64 = (o["status"].cpu().numpy() for o in (one, fb, f64))
