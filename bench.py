@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--batch", type=int, default=0,
+                   help="solve only the first N reactors of the workload's batch (profiling captures)")
     return p.parse_args()
 
 
@@ -258,6 +260,8 @@ def run_ours(args):
     from paper_2005_11468_gb300 import shard
     batch = synth.make_batch(spec, w["B"], seed=shard.shard_seed(synth.MECH_SEED_BASE + 10 * w["tag"] + 1, rank),
                              tau_range=w.get("tau_range", (1e-4, 1e-2)))
+    if args.batch:
+        batch = batch.subset(range(min(args.batch, batch.B)))
     t = {k: torch.tensor(getattr(batch, k), dtype=torch.float64, device=dev)
          for k in ("Y_in", "T_in", "tau", "P", "Y0", "T0")}
     soot = spec.soot is not None
