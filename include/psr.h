@@ -110,7 +110,10 @@ typedef struct {
     int32_t mixed_max_newton; /* 300: Newton cap of the FP32-Jacobian launch when the FP64
                                re-solve follows (0 = max_newton); reactors it leaves are
                                re-solved in FP64 with max_newton */
-    int32_t reserved[4];
+    int32_t jac_age;        /* 1 (default): a fresh Jacobian and LU every Newton iteration;
+                               A > 1: the factors serve up to A iterations while undamped steps
+                               keep shrinking (any failure retries with fresh factors) */
+    int32_t reserved[3];
 } psr_options;
 
 void psr_options_default(psr_options *o);

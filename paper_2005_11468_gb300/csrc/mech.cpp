@@ -538,6 +538,7 @@ void psr_options_default(psr_options *o) {
     o->mixed_fallback = 1;
     o->jacobian = PSR_JAC_ANALYTIC;
     o->mixed_max_newton = 300;
+    o->jac_age = 1;
 }
 
 }  // extern "C"

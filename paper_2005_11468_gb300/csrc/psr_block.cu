@@ -783,13 +783,35 @@ __device__ bool b_damped_newton(BCtx &cx, const BWS<TJ> &w, double *y, const dou
     // ||F||_inf of the steady residual at the first and the last evaluated point
     if (fnorm) fnorm[0] = fnorm[1] = bmax(t < n ? fabs(w.F[t]) : 0.0, w.red);
     double dn_prev = INFINITY;
+    // Jacobian reuse (o.jac_age > 1), as in the warp solver
+    bool have_lu = false, at_y = true;
+    int age = 0;
     for (int it = 0; it < max_it; ++it) {
         if (counter >= o.max_newton) break;
         ++counter;
-        b_eval_J(cx.M, w, c, cx.mx, cx.tau, o.energy, cx.mult);
-        if (!b_lu(w, n)) break;
+        bool fresh = false;
+        if (!have_lu || age + 1 >= o.jac_age) {
+            if (!at_y) {   // the last residual was a rejected trial: the Jacobian needs y's caches
+                b_residual_R(cx, w, y, c, xref, w.F, w.R);
+                if (fnorm) fnorm[1] = bmax(t < n ? fabs(w.F[t]) : 0.0, w.red);
+                at_y = true;
+            }
+            b_eval_J(cx.M, w, c, cx.mx, cx.tau, o.energy, cx.mult);
+            if (!b_lu(w, n)) break;
+            have_lu = true;
+            age = 0;
+            fresh = true;
+        } else {
+            ++age;
+        }
         b_lu_solve_neg(w, n, w.R, w.dy);
-        if (!b_all_finite(w.dy, n)) break;
+        if (!b_all_finite(w.dy, n)) {
+            if (!fresh) {
+                have_lu = false;
+                continue;
+            }
+            break;
+        }
         bool done;
         if (steady) {
             const double rmax = bmax(t < n ? fabs(w.R[t]) : 0.0, w.red);
@@ -803,8 +825,13 @@ __device__ bool b_damped_newton(BCtx &cx, const BWS<TJ> &w, double *y, const dou
             return true;
         }
         const double dn = b_scaled_max(w.dy, y, K, n, w.red);
-        if (dn >= dn_prev) break;
-        dn_prev = dn;
+        if (dn >= dn_prev) {
+            if (!fresh) {
+                have_lu = false;
+                continue;
+            }
+            break;
+        }
         double lam = fmin(1.0, b_max_in_bounds(y, w.dy, K, o, w.red));
         bool accepted = false;
         for (int d = 0; d < o.max_damp; ++d) {
@@ -812,6 +839,7 @@ __device__ bool b_damped_newton(BCtx &cx, const BWS<TJ> &w, double *y, const dou
             __syncthreads();
             if (b_in_bounds(w.yt, K, o)) {
                 b_residual_R(cx, w, w.yt, c, xref, w.F, w.Rt);
+                at_y = false;
                 if (fnorm) fnorm[1] = bmax(t < n ? fabs(w.F[t]) : 0.0, w.red);
                 if (b_all_finite(w.Rt, n)) {
                     b_lu_solve_neg(w, n, w.Rt, w.db);
@@ -823,12 +851,21 @@ __device__ bool b_damped_newton(BCtx &cx, const BWS<TJ> &w, double *y, const dou
             }
             lam *= 0.5;
         }
-        if (!accepted) break;
+        if (!accepted) {
+            if (!fresh) {
+                have_lu = false;
+                continue;
+            }
+            break;
+        }
+        dn_prev = dn;
         if (t < n) {
             y[t] = w.yt[t];
             w.R[t] = w.Rt[t];
         }
         __syncthreads();
+        at_y = true;
+        if (lam < 1.0) have_lu = false;   // a damped step: fresh factors next
     }
     return false;
 }

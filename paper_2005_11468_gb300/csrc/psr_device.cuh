@@ -89,6 +89,7 @@ struct Opts {
     int max_newton, max_damp, max_ts_rounds, ts_steps, ts_newton, energy;
     int jac_fd;   // Jacobian by central differences (the paper's method) instead of analytic
     int mixed_max_newton;   // Newton cap of the FP32-Jacobian launch when the FP64 re-solve follows
+    int jac_age;            // iterations one Jacobian factorisation may serve (1 = fresh each time)
 };
 
 // Scalars of the last residual evaluation that the Jacobian reuses.

@@ -958,17 +958,42 @@ __device__ bool damped_newton(Ctx &cx, const WS<TJ> &w, V2 &y, const V2 &xref, c
     // ||F||_inf of the steady residual at the first and the last evaluated point
     if (fnorm) fnorm[0] = fnorm[1] = wmax(fmax(fabs(F.a), fabs(F.b)));
     double dn_prev = INFINITY;
+    // Jacobian reuse (o.jac_age > 1): the LU factors serve up to jac_age iterations while
+    // undamped steps keep shrinking; any failure with old factors retries with fresh ones
+    bool have_lu = false, at_y = true;
+    int age = 0;
     for (int it = 0; it < max_it; ++it) {
         if (counter >= o.max_newton) break;
         ++counter;
-        if constexpr (FDJ)
-            eval_J_fd<TJ>(cx.M, w, y, c, cx.mx, cx.sl, cx.r.Yin, cx.r.tau, cx.r.P, cx.r.Tspec, o.energy, cx.mult);
-        else
-            eval_J<TJ, SOOT>(cx.M, w, y, c, cx.mx, cx.sl, cx.r.Yin, cx.r.Min, cx.r.tau, o.energy, cx.mult);
-        if (!lu_factor(w, n)) break;
+        bool fresh = false;
+        if (!have_lu || age + 1 >= o.jac_age) {
+            if (!at_y) {   // the last residual was a rejected trial: the Jacobian needs y's caches
+                V2 Fy;
+                residual_R<TJ, SOOT>(cx, w, y, c, xref, Fy, R);
+                if (fnorm) fnorm[1] = wmax(fmax(fabs(Fy.a), fabs(Fy.b)));
+                at_y = true;
+            }
+            if constexpr (FDJ)
+                eval_J_fd<TJ>(cx.M, w, y, c, cx.mx, cx.sl, cx.r.Yin, cx.r.tau, cx.r.P, cx.r.Tspec, o.energy,
+                              cx.mult);
+            else
+                eval_J<TJ, SOOT>(cx.M, w, y, c, cx.mx, cx.sl, cx.r.Yin, cx.r.Min, cx.r.tau, o.energy, cx.mult);
+            if (!lu_factor(w, n)) break;
+            have_lu = true;
+            age = 0;
+            fresh = true;
+        } else {
+            ++age;
+        }
         V2 dy;
         lu_solve_neg(w, n, R, dy);
-        if (!all_finite(dy)) break;
+        if (!all_finite(dy)) {
+            if (!fresh) {
+                have_lu = false;
+                continue;
+            }
+            break;
+        }
         if (steady) {
             const double rmax = wmax(fmax(fabs(R.a), fabs(R.b)));
             if (rmax <= o.ftol && step_small(dy, y, K, n, o.step_rtol, o.step_atol_y, o.step_atol_t, o.step_rtol)) {
@@ -980,8 +1005,13 @@ __device__ bool damped_newton(Ctx &cx, const WS<TJ> &w, V2 &y, const V2 &xref, c
             return true;
         }
         const double dn = scaled_max(dy, y, K, n);
-        if (dn >= dn_prev) break;
-        dn_prev = dn;
+        if (dn >= dn_prev) {
+            if (!fresh) {
+                have_lu = false;
+                continue;
+            }
+            break;
+        }
         double lam = fmin(1.0, max_in_bounds(y, dy, K, o));
         bool accepted = false;
         V2 yt, Rt;
@@ -990,6 +1020,7 @@ __device__ bool damped_newton(Ctx &cx, const WS<TJ> &w, V2 &y, const V2 &xref, c
             if (in_bounds(yt, K, o)) {
                 V2 Ft;
                 residual_R<TJ, SOOT>(cx, w, yt, c, xref, Ft, Rt);
+                at_y = false;
                 if (fnorm) fnorm[1] = wmax(fmax(fabs(Ft.a), fabs(Ft.b)));
                 if (all_finite(Rt)) {
                     V2 db;
@@ -1002,9 +1033,18 @@ __device__ bool damped_newton(Ctx &cx, const WS<TJ> &w, V2 &y, const V2 &xref, c
             }
             lam *= 0.5;
         }
-        if (!accepted) break;
+        if (!accepted) {
+            if (!fresh) {
+                have_lu = false;
+                continue;
+            }
+            break;
+        }
+        dn_prev = dn;
         y = yt;
         R = Rt;
+        at_y = true;
+        if (lam < 1.0) have_lu = false;   // a damped step: fresh factors next
     }
     return false;
 }
@@ -1491,6 +1531,7 @@ Opts to_opts(const psr_options *po) {
     o.ts_newton = s.ts_newton;
     o.jac_fd = s.jacobian;
     o.mixed_max_newton = s.mixed_max_newton;
+    o.jac_age = s.jac_age < 1 ? 1 : s.jac_age;
     o.energy = s.energy;
     return o;
 }
@@ -1505,7 +1546,8 @@ int check_opts(const psr_options *po) {
         (s.precision != PSR_FP64 && s.precision != PSR_MIXED) ||
         (s.energy != PSR_ADIABATIC && s.energy != PSR_FIXED_T) || s.warps_per_block < 0 || s.warps_per_block > 32 ||
         s.blocks_per_sm < 0 || (s.mixed_fallback != 0 && s.mixed_fallback != 1) ||
-        (s.jacobian != PSR_JAC_ANALYTIC && s.jacobian != PSR_JAC_FD) || s.mixed_max_newton < 0)
+        (s.jacobian != PSR_JAC_ANALYTIC && s.jacobian != PSR_JAC_FD) || s.mixed_max_newton < 0 || s.jac_age < 0 ||
+        s.jac_age > 64)
         return set_error(PSR_E_ARG, "psr_options: value out of range");
     return PSR_OK;
 }

@@ -394,3 +394,26 @@ def test_fd_jacobian_solves_reach_the_same_roots(dev):
     assert np.all(f["fnorm"].cpu().numpy()[sf == 0] <= 1e-8)
     with pytest.raises(psr.PsrError):
         psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"], opts=psr.Options(jacobian=7))
+
+
+@pytest.mark.parametrize("name,n", [("k10_b64", 64), ("k200_b2048", 12)])
+def test_jacobian_reuse_reaches_roots_of_the_oracle(dev, name, n):
+    """Newton with factors kept for up to `jac_age` iterations (warp path at K = 10, block
+    path at K = 200) stops only at points the oracle's residual calls steady states."""
+    _, mech, batch = workload(name)
+    batch = batch.subset(range(n))
+    t = to_dev(batch, dev)
+    gm = gpu_mech(name)
+    a = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"])
+    r = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"], opts=psr.Options(jac_age=2))
+    sr = r["status"].cpu().numpy()
+    Yr, Tr = r["Y"].cpu().numpy(), r["T"].cpu().numpy()
+    ok = np.isin(sr, psr.CONVERGED_STATES)
+    assert ok.mean() >= 0.9
+    for b in np.flatnonzero(ok):
+        F = O.gas_residual(mech, np.r_[Yr[b], Tr[b]][None], O.inlet_of(batch, b))[0]
+        assert np.max(np.abs(F)) <= 1e-7, f"reactor {b}: |F| {np.max(np.abs(F)):.2e}"
+    same = ok & (np.abs(Tr - a["T"].cpu().numpy()) <= 1e-6)
+    assert same.sum() >= 0.8 * ok.sum()
+    with pytest.raises(psr.PsrError):
+        psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"], opts=psr.Options(jac_age=65))
