@@ -113,7 +113,12 @@ typedef struct {
     int32_t jac_age;        /* 1 (default): a fresh Jacobian and LU every Newton iteration;
                                A > 1: the factors serve up to A iterations while undamped steps
                                keep shrinking (any failure retries with fresh factors) */
-    int32_t reserved[3];
+    int32_t ts_linear;      /* 150: while a reactor has used fewer Newton iterations than this,
+                               each pseudo-time step is one linearised Newton iteration
+                               (pseudo-transient continuation; dt grown by 2 x the ||F|| ratio
+                               clipped to [0.1, 8]); later steps, and all steps when 0, are
+                               solved by damped Newton (<= ts_newton iterations, to ts_rtol) */
+    int32_t reserved[2];
 } psr_options;
 
 void psr_options_default(psr_options *o);

@@ -34,6 +34,7 @@ N_A = 6.02214076e23       # 1/mol
 K_B = 1.380649e-16        # erg/K
 M_C = 12.011 / N_A        # g per carbon atom
 NMOM = 6
+ZETA_STEP = 3.0           # largest change of a log moment ln(M_r/s_r) in one Newton step
 
 
 class Soot:
@@ -178,7 +179,12 @@ class SootSystem(O.GasSystem):
         return np.r_[super().norm_weights(x[:self.K + 1]), np.ones(NMOM)]
 
     def max_in_bounds(self, x, dx, opts):
-        return super().max_in_bounds(x[:self.K + 1], dx[:self.K + 1], opts)
+        """The gas bounds, and no log moment moving by more than ZETA_STEP in one step:
+        larger moves (undamped pseudo-time steps at large dt) can leave a moment set outside
+        the range where the interpolative closure is defined."""
+        lam = super().max_in_bounds(x[:self.K + 1], dx[:self.K + 1], opts)
+        dz = float(np.max(np.abs(dx[self.K + 1:])))
+        return min(lam, ZETA_STEP / dz) if dz > ZETA_STEP else lam
 
     def in_bounds(self, x, opts):
         return super().in_bounds(x[:self.K + 1], opts)

@@ -337,6 +337,9 @@ class Options:
     max_ts_rounds: int = 100    # Newton attempts that may be followed by time stepping
     ts_steps: int = 12          # pseudo-time steps per round before Newton is retried
     ts_newton: int = 8          # Newton iterations allowed per pseudo-time step
+    ts_linear: int = 150        # pseudo-time steps are linearised (one Newton iteration each)
+                                #   while fewer iterations than this have been used; later
+                                #   ones (all when 0) are solved by damped Newton to ts_rtol
     ts_rtol: float = 1e-4       # a time step is solved when its undamped step is below
     ts_atol_y: float = 1e-10    #   ts_rtol |x_j| + ts_atol_j
     dt0_over_tau: float = 1e-10
@@ -503,17 +506,48 @@ def _damped_newton(system, x, c, x_ref, max_it, opts, steady, counter, fnorm=Non
     return y, system.F(y)[0], False
 
 
+def _linearised_step(system, x, c, opts, counter):
+    """One linearised backward-Euler step of dx/dt = -D F(x) / tau (pseudo-transient
+    continuation, Kelley & Keyes 1998): solve (J(x) + diag(c)) dx = -F(x) and take the
+    full step when it keeps the iterate in bounds and F finite. Returns (x_new,
+    ||F(x_new)||_inf, accepted)."""
+    if counter[0] >= opts.max_newton:
+        return x, None, False
+    counter[0] += 1
+    F = system.F(x)[0]
+    LU, piv, ok = lu_factor(jacobian_cs(system, x) + np.diag(c))
+    if not ok:
+        return x, None, False
+    dx = lu_solve(LU, piv, -F)
+    if not np.all(np.isfinite(dx)) or system.max_in_bounds(x, dx, opts) < 1.0:
+        return x, None, False
+    y = x + dx
+    if not system.in_bounds(y, opts):
+        return x, None, False
+    Fy = system.F(y)[0]
+    if not np.all(np.isfinite(Fy)):
+        return x, None, False
+    return y, float(np.max(np.abs(Fy))), True
+
+
 def solve_system(system, x0, opts: Options = Options()):
     """Hybrid Newton / pseudo-transient solve of F(x) = 0 (Sec. 3): a damped Newton
     iteration on the steady problem; when it fails (damping exhausted, corrections
     not shrinking, singular J) the estimate it started from is conditioned by
-    ts_steps backward-Euler steps of the transient form dx/dt = -D F(x) / tau, each
-    solved by damped Newton; after an accepted step dt grows by 2 if the step took
-    <= 3 iterations (1.25 after 4, 1 after more), times the factor by which the step
-    reduced ||F||_inf, clipped to [1, 4] (switched evolution relaxation, Mulder & van
-    Leer 1985; ||F||_inf taken at the last point each Newton evaluated), and shrinks by
-    dt_shrink after a failed step; then Newton is tried again. iters counts every
-    Newton iteration (one Jacobian and LU each), ts_steps the accepted pseudo-time steps."""
+    ts_steps backward-Euler steps of the transient form dx/dt = -D F(x) / tau; then
+    Newton is tried again.
+
+    While fewer than ts_linear Newton iterations have been used, each step is one
+    linearised Newton iteration (pseudo-transient continuation, Kelley & Keyes 1998); after
+    an accepted step dt grows by 2 times the factor by which the step changed ||F||_inf,
+    clipped to [0.1, 8] (switched evolution relaxation, Mulder & van Leer 1985), and shrinks
+    by dt_shrink after a rejected one.
+    Later steps are solved by damped Newton (<= ts_newton iterations, to ts_rtol);
+    after an accepted step dt grows by 2 if it took <= 3 iterations (1.25 after 4, 1
+    after more), times the ||F||_inf reduction clipped to [1, 4] (||F||_inf at the last
+    point each Newton evaluated).
+    iters counts every Newton iteration (one Jacobian and LU each), ts_steps the
+    accepted pseudo-time steps."""
     tau = system.inlet.tau
     x = np.array(x0, dtype=np.float64)
     F = system.F(x)[0]
@@ -540,8 +574,13 @@ def solve_system(system, x0, opts: Options = Options()):
         while taken < opts.ts_steps:
             c = tau / dt * system.transient_weights(x)
             used = counter[0]
-            fs = [None, None]
-            y, Fy, conv = _damped_newton(system, x, c, x, opts.ts_newton, opts, False, counter, fs)
+            linear = counter[0] < opts.ts_linear
+            if linear:
+                y, f_new, conv = _linearised_step(system, x, c, opts, counter)
+            else:
+                fs = [None, None]
+                y, Fy, conv = _damped_newton(system, x, c, x, opts.ts_newton, opts, False, counter, fs)
+                f_new = fs[1]
             used = counter[0] - used
             if counter[0] >= opts.max_newton:
                 return Result(x, MAX_ITER, counter[0], ts, float(np.max(np.abs(system.F(x)[0]))))
@@ -549,11 +588,14 @@ def solve_system(system, x0, opts: Options = Options()):
                 x = y
                 taken += 1
                 ts += 1
-                # grow dt by how easily the step was solved and how much it reduced ||F||
-                g = 2.0 if used <= 3 else (1.25 if used == 4 else 1.0)
-                if fs[1] is not None and fs[1] > 0.0 and f_prev is not None:
-                    g *= min(4.0, max(1.0, f_prev / fs[1]))
-                f_prev = fs[1]
+                if linear:
+                    g = 2.0 * (min(8.0, max(0.1, f_prev / f_new)) if f_new > 0.0 else 1.0)
+                else:
+                    # grow dt by how easily the step was solved and how much it reduced ||F||
+                    g = 2.0 if used <= 3 else (1.25 if used == 4 else 1.0)
+                    if f_new is not None and f_new > 0.0 and f_prev is not None:
+                        g *= min(4.0, max(1.0, f_prev / f_new))
+                f_prev = f_new
                 dt = min(g * dt, 1e6 * tau)
             else:
                 dt *= opts.dt_shrink

@@ -539,6 +539,7 @@ void psr_options_default(psr_options *o) {
     o->jacobian = PSR_JAC_ANALYTIC;
     o->mixed_max_newton = 300;
     o->jac_age = 1;
+    o->ts_linear = 150;
 }
 
 }  // extern "C"

@@ -869,6 +869,38 @@ __device__ bool b_damped_newton(BCtx &cx, const BWS<TJ> &w, double *y, const dou
     }
     return false;
 }
+// One linearised backward-Euler step from x (w.x) with the diagonal shift in w.c, the
+// warp solver's linear_step: (J(x) + diag c) dx = -F(x), the full step taken when it stays
+// in bounds and F stays finite. fx_valid: w.F holds F(x) and the caches are x's.
+template <class TJ>
+__device__ bool b_linear_step(BCtx &cx, const BWS<TJ> &w, int &counter, bool &fx_valid, double &f_new) {
+    const int t = threadIdx.x;
+    const int K = cx.K, n = cx.n;
+    const Opts &o = cx.o;
+    if (counter >= o.max_newton) return false;
+    ++counter;
+    if (!fx_valid) b_residual_R(cx, w, w.x, w.c, w.x, w.F, w.R);
+    fx_valid = false;   // the Jacobian consumes the rate caches
+    b_eval_J(cx.M, w, w.c, cx.mx, cx.tau, o.energy, cx.mult);
+    if (!b_lu(w, n)) return false;
+    b_lu_solve_neg(w, n, w.F, w.dy);
+    if (!b_all_finite(w.dy, n)) return false;
+    if (b_max_in_bounds(w.x, w.dy, K, o, w.red) < 1.0) return false;
+    if (t < n) w.yt[t] = w.x[t] + w.dy[t];
+    __syncthreads();
+    if (!b_in_bounds(w.yt, K, o)) return false;
+    b_residual_R(cx, w, w.yt, w.c, w.yt, w.Rt, w.db);
+    if (!b_all_finite(w.Rt, n)) return false;
+    f_new = bmax(t < n ? fabs(w.Rt[t]) : 0.0, w.red);
+    if (t < n) {
+        w.x[t] = w.yt[t];
+        w.F[t] = w.Rt[t];
+    }
+    __syncthreads();
+    fx_valid = true;
+    return true;
+}
+
 
 __device__ void b_inlet_enthalpy(BCtx &cx, double Tin, double *red) {
     const int t = threadIdx.x;
@@ -941,6 +973,7 @@ __device__ void b_solve_one(BCtx &cx, const BWS<TJ> &w, const Batch &bt, int64_t
             int taken = 0;
             bool done = false;
             double f_prev = fn[0];   // ||F(x)||_inf of the estimate being conditioned
+            bool fx_valid = false;   // the steady attempt left the caches elsewhere
             while (taken < o.ts_steps) {
                 const double Tx = w.x[K];
                 const double s = tau / dt;
@@ -952,8 +985,20 @@ __device__ void b_solve_one(BCtx &cx, const BWS<TJ> &w, const Batch &bt, int64_t
                 }
                 __syncthreads();
                 const int used0 = counter;
-                double fs[2];
-                const bool ok = b_damped_newton(cx, w, w.y, w.x, w.c, o.ts_newton, false, counter, fs);
+                double f_new = 0.0;
+                bool ok;
+                const bool linear = counter < o.ts_linear;
+                if (linear) {
+                    ok = b_linear_step(cx, w, counter, fx_valid, f_new);   // updates w.x itself
+                } else {
+                    double fs[2];
+                    ok = b_damped_newton(cx, w, w.y, w.x, w.c, o.ts_newton, false, counter, fs);
+                    f_new = fs[1];
+                    if (ok) {
+                        if (t < n) w.x[t] = w.y[t];
+                        __syncthreads();
+                    }
+                }
                 const int used = counter - used0;
                 if (counter >= o.max_newton) {
                     status = PSR_MAX_ITER;
@@ -962,15 +1007,17 @@ __device__ void b_solve_one(BCtx &cx, const BWS<TJ> &w, const Batch &bt, int64_t
                     break;
                 }
                 if (ok) {
-                    if (t < n) w.x[t] = w.y[t];
-                    __syncthreads();
                     ++taken;
                     ++ts;
-                    // growth by how easily the step was solved, times its reduction of ||F||
-                    // clipped to [1, 4] (switched evolution relaxation)
-                    double g = (used <= 3) ? 2.0 : (used == 4 ? 1.25 : 1.0);
-                    if (fs[1] > 0.0) g *= fmin(4.0, fmax(1.0, f_prev / fs[1]));
-                    f_prev = fs[1];
+                    // switched evolution relaxation: dt follows the step's change of ||F||
+                    double g;
+                    if (linear) {
+                        g = 2.0 * (f_new > 0.0 ? fmin(8.0, fmax(0.1, f_prev / f_new)) : 1.0);
+                    } else {   // Newton-solved steps: also by how easily the step was solved
+                        g = (used <= 3) ? 2.0 : (used == 4 ? 1.25 : 1.0);
+                        if (f_new > 0.0) g *= fmin(4.0, fmax(1.0, f_prev / f_new));
+                    }
+                    f_prev = f_new;
                     dt = fmin(g * dt, 1e6 * tau);
                 } else {
                     dt *= o.dt_shrink;
@@ -1204,6 +1251,13 @@ int launch_block(const Mech &m, const Batch &bt, const Opts &o, int bps_req, cud
 }
 
 }  // namespace
+
+// FP64 re-solve, one block per reactor, of the reactors a warp-solver launch listed (bt.list):
+// a short list would leave the GPU almost idle under the warp solver, where one reactor
+// takes a warp for all of its iterations.
+int block_resolve_list(const Mech &m, const Batch &bt, const Opts &o, cudaStream_t st, int *queue) {
+    return launch_block<double>(m, bt, o, 0, st, queue);
+}
 
 int block_check(const Mech &m) {
     if (m.dev.nsoot) return set_error(PSR_E_UNSUPPORTED, "soot moments need K + 7 <= 64 (warp solver)");

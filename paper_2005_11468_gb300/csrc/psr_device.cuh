@@ -13,6 +13,7 @@ namespace psr {
 constexpr unsigned kFull = 0xffffffffu;
 
 
+constexpr double kZetaStep = 3.0;   // largest change of a log moment in one Newton step
 constexpr double kLn10 = 2.302585092994045684;
 
 // ---------------------------------------------------------------- warp helpers
@@ -90,6 +91,7 @@ struct Opts {
     int jac_fd;   // Jacobian by central differences (the paper's method) instead of analytic
     int mixed_max_newton;   // Newton cap of the FP32-Jacobian launch when the FP64 re-solve follows
     int jac_age;            // iterations one Jacobian factorisation may serve (1 = fresh each time)
+    int ts_linear;          // linearised pseudo-time steps while the iteration count is below this
 };
 
 // Scalars of the last residual evaluation that the Jacobian reuses.
@@ -185,6 +187,7 @@ __device__ __forceinline__ Troe troe_eval(const double *__restrict__ tp, double 
 // Host launchers of the block-per-reactor solver (psr_block.cu), for mechanisms whose
 // K + 1 unknowns exceed one warp's 64.
 int block_check(const Mech &m);
+int block_resolve_list(const Mech &m, const Batch &bt, const Opts &o, cudaStream_t st, int *queue);
 int block_solve(const Mech &m, const Batch &bt, const Opts &o, int precision, bool fallback, int bps_req,
                 cudaStream_t st);
 int block_eval(const Mech &m, const Batch &bt, int energy, int want_J, int precision, double *out, cudaStream_t st,

@@ -895,13 +895,19 @@ __device__ __forceinline__ bool in_bounds(const V2 &y, int K, const Opts &o) {
     return __all_sync(kFull, ok);
 }
 
-__device__ __forceinline__ double max_in_bounds(const V2 &y, const V2 &dy, int K, const Opts &o) {
+// Largest step fraction that keeps Y_k >= -y_floor and t_min <= T <= t_max, and moves no
+// log moment by more than kZetaStep (moment sets stay in the range where the interpolative
+// closure is defined).
+__device__ __forceinline__ double max_in_bounds(const V2 &y, const V2 &dy, int K, int n, const Opts &o) {
     const int lane = threadIdx.x & 31;
     double lam = INFINITY;
     for (int h = 0; h < 2; ++h) {
         int j = lane + 32 * h;
-        if (j > K) continue;
         const double x = h ? y.b : y.a, d = h ? dy.b : dy.a;
+        if (j > K) {
+            if (j < n && fabs(d) > kZetaStep) lam = fmin(lam, kZetaStep / fabs(d));
+            continue;
+        }
         const double lo = (j < K) ? -o.y_floor : o.t_min, hi = (j < K) ? INFINITY : o.t_max;
         if (d < 0 && x + d < lo) lam = fmin(lam, (lo - x) / d);
         else if (d > 0 && x + d > hi) lam = fmin(lam, (hi - x) / d);
@@ -1012,7 +1018,7 @@ __device__ bool damped_newton(Ctx &cx, const WS<TJ> &w, V2 &y, const V2 &xref, c
             }
             break;
         }
-        double lam = fmin(1.0, max_in_bounds(y, dy, K, o));
+        double lam = fmin(1.0, max_in_bounds(y, dy, K, n, o));
         bool accepted = false;
         V2 yt, Rt;
         for (int d = 0; d < o.max_damp; ++d) {
@@ -1047,6 +1053,43 @@ __device__ bool damped_newton(Ctx &cx, const WS<TJ> &w, V2 &y, const V2 &xref, c
         if (lam < 1.0) have_lu = false;   // a damped step: fresh factors next
     }
     return false;
+}
+
+// One linearised backward-Euler step of dx/dt = -D F / tau from x (pseudo-transient
+// continuation): (J(x) + diag c) dx = -F(x), the full step taken when it stays in bounds
+// and F stays finite. fx_valid: Fx holds F(x) and the rate caches are x's (true after an
+// accepted step; the Jacobian consumes the caches). f_new = ||F||_inf at the new x.
+template <class TJ, bool SOOT, bool FDJ = false>
+__device__ bool linear_step(Ctx &cx, const WS<TJ> &w, V2 &x, V2 &Fx, bool &fx_valid, const V2 &c, int &counter,
+                            double &f_new) {
+    const int K = cx.K, n = cx.n;
+    const Opts &o = cx.o;
+    if (counter >= o.max_newton) return false;
+    ++counter;
+    const V2 zero{0.0, 0.0};
+    if (!fx_valid) {
+        V2 R;
+        residual_R<TJ, SOOT>(cx, w, x, zero, x, Fx, R);
+    }
+    fx_valid = false;
+    if constexpr (FDJ)
+        eval_J_fd<TJ>(cx.M, w, x, c, cx.mx, cx.sl, cx.r.Yin, cx.r.tau, cx.r.P, cx.r.Tspec, o.energy, cx.mult);
+    else
+        eval_J<TJ, SOOT>(cx.M, w, x, c, cx.mx, cx.sl, cx.r.Yin, cx.r.Min, cx.r.tau, o.energy, cx.mult);
+    if (!lu_factor(w, n)) return false;
+    V2 dx;
+    lu_solve_neg(w, n, Fx, dx);
+    if (!all_finite(dx) || max_in_bounds(x, dx, K, n, o) < 1.0) return false;
+    const V2 xt = axpy(x, 1.0, dx);
+    if (!in_bounds(xt, K, o)) return false;
+    V2 Ft, R;
+    residual_R<TJ, SOOT>(cx, w, xt, zero, xt, Ft, R);
+    if (!all_finite(Ft)) return false;
+    f_new = wmax(fmax(fabs(Ft.a), fabs(Ft.b)));
+    x = xt;
+    Fx = Ft;
+    fx_valid = true;
+    return true;
 }
 
 // Initial log moments: the given M0, or the nucleation-only steady state at the initial
@@ -1154,6 +1197,8 @@ __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) 
             int taken = 0;
             bool done = false;
             double f_prev = fn[0];   // ||F(x)||_inf of the estimate being conditioned
+            bool fx_valid = false;   // the steady attempt left the caches elsewhere
+            V2 Fx = F;
             while (taken < o.ts_steps) {
                 const double Tx = comp_get(x, K);
                 const double s = tau / dt;
@@ -1163,8 +1208,16 @@ __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) 
                 c.b = (lane + 32 < K) ? s : (lane + 32 == K ? sT : (lane + 32 < cx.n ? s : 0.0));
                 const int used0 = counter;
                 V2 y = x;
-                double fs[2];
-                bool ok = damped_newton<TJ, SOOT, FDJ>(cx, w, y, x, c, o.ts_newton, false, counter, fs);
+                double f_new = 0.0;
+                bool ok;
+                const bool linear = counter < o.ts_linear;
+                if (linear) {
+                    ok = linear_step<TJ, SOOT, FDJ>(cx, w, y, Fx, fx_valid, c, counter, f_new);
+                } else {
+                    double fs[2];
+                    ok = damped_newton<TJ, SOOT, FDJ>(cx, w, y, x, c, o.ts_newton, false, counter, fs);
+                    f_new = fs[1];
+                }
                 const int used = counter - used0;
                 if (counter >= o.max_newton) {
                     status = PSR_MAX_ITER;
@@ -1176,11 +1229,15 @@ __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) 
                     x = y;
                     ++taken;
                     ++ts;
-                    // growth by how easily the step was solved, times its reduction of ||F||
-                    // clipped to [1, 4] (switched evolution relaxation)
-                    double g = (used <= 3) ? 2.0 : (used == 4 ? 1.25 : 1.0);
-                    if (fs[1] > 0.0) g *= fmin(4.0, fmax(1.0, f_prev / fs[1]));
-                    f_prev = fs[1];
+                    // switched evolution relaxation: dt follows the step's change of ||F||
+                    double g;
+                    if (linear) {
+                        g = 2.0 * (f_new > 0.0 ? fmin(8.0, fmax(0.1, f_prev / f_new)) : 1.0);
+                    } else {   // Newton-solved steps: also by how easily the step was solved
+                        g = (used <= 3) ? 2.0 : (used == 4 ? 1.25 : 1.0);
+                        if (f_new > 0.0) g *= fmin(4.0, fmax(1.0, f_prev / f_new));
+                    }
+                    f_prev = f_new;
                     dt = fmin(g * dt, 1e6 * tau);
                 } else {
                     dt *= o.dt_shrink;
@@ -1532,6 +1589,7 @@ Opts to_opts(const psr_options *po) {
     o.jac_fd = s.jacobian;
     o.mixed_max_newton = s.mixed_max_newton;
     o.jac_age = s.jac_age < 1 ? 1 : s.jac_age;
+    o.ts_linear = s.ts_linear;
     o.energy = s.energy;
     return o;
 }
@@ -1547,7 +1605,7 @@ int check_opts(const psr_options *po) {
         (s.energy != PSR_ADIABATIC && s.energy != PSR_FIXED_T) || s.warps_per_block < 0 || s.warps_per_block > 32 ||
         s.blocks_per_sm < 0 || (s.mixed_fallback != 0 && s.mixed_fallback != 1) ||
         (s.jacobian != PSR_JAC_ANALYTIC && s.jacobian != PSR_JAC_FD) || s.mixed_max_newton < 0 || s.jac_age < 0 ||
-        s.jac_age > 64)
+        s.jac_age > 64 || s.ts_linear < 0)
         return set_error(PSR_E_ARG, "psr_options: value out of range");
     return PSR_OK;
 }
@@ -1641,7 +1699,11 @@ int launch_mixed(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int
         b2.list = list;
         b2.list_len = len;
         b2.fallback = 1;
-        rc = launch_solve_q<double>(m, b2, o, wpb_req, bps_req, st, q1);
+        // the list is short: gas-phase reactors go to the block solver, one CTA each
+        if (!m.dev.nsoot && block_check(m) == PSR_OK)
+            rc = block_resolve_list(m, b2, o, st, q1);
+        else
+            rc = launch_solve_q<double>(m, b2, o, wpb_req, bps_req, st, q1);
     }
     cudaFreeAsync(scr, st);
     return rc;

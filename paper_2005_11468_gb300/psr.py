@@ -48,7 +48,7 @@ class COptions(ctypes.Structure):
                 ("energy", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("mixed_fallback", ctypes.c_int32),
                 ("jacobian", ctypes.c_int32), ("mixed_max_newton", ctypes.c_int32),
-                ("jac_age", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("jac_age", ctypes.c_int32), ("ts_linear", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 _lib = None
@@ -123,6 +123,7 @@ class Options:
     jacobian: int = 0
     mixed_max_newton: int = 300
     jac_age: int = 1
+    ts_linear: int = 150
 
     def to_c(self):
         o = COptions()

@@ -190,6 +190,26 @@ def test_solve_parity_k53_full_size_sampled(dev, precision):
     compare_roots("k53_b4096", idx, ref, Y[idx], T[idx], st[idx], f"k53 prec={precision}")
 
 
+def test_mixed_fallback_through_the_block_solver_k53(dev):
+    """The mixed form's FP64 re-solve of the reactors its FP32-Jacobian launch left runs one
+    block per reactor (n = 54 here, below the sizes the block solver otherwise takes): with
+    the FP32 launch capped at 40 iterations most reactors take that path, and the sampled
+    ones match the oracle."""
+    _, mech, batch = workload("k53_b4096")
+    t = to_dev(batch, dev)
+    out = psr.batch_solve(gpu_mech("k53_b4096"), t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"],
+                          opts=psr.Options(precision=psr.PSR_MIXED, mixed_max_newton=40))
+    Y, T, st = out["Y"].cpu().numpy(), out["T"].cpu().numpy(), out["status"].cpu().numpy()
+    assert np.mean(st == psr.PSR_REFINE_FALLBACK) >= 0.5
+    conv = np.isin(st, psr.CONVERGED_STATES)
+    assert conv.mean() >= 0.999
+    assert np.all(out["fnorm"].cpu().numpy()[conv] <= 1e-8)
+    idx = [int(i) for i in np.random.Generator(np.random.PCG64(5)).choice(batch.B, 6, replace=False)]
+    ref = oracle_solution("k53_b4096", idx)
+    assert np.any(st[idx] == psr.PSR_REFINE_FALLBACK)
+    compare_roots("k53_b4096", idx, ref, Y[idx], T[idx], st[idx], "k53 block re-solve")
+
+
 def test_fixed_temperature_closed_forms(dev):
     """Golden isomerisation and dimerisation (fixed T) against their closed forms."""
     import torch
@@ -278,7 +298,9 @@ def test_edge_cases(dev):
 
 def test_autotune_picks_a_shape_with_identical_results(dev):
     """psr_autotune returns one of its candidate launch shapes; solving with it gives the
-    default shape's results bit for bit (one warp per reactor either way)."""
+    default shape's results: bit for bit where the warp solver converged (one warp per
+    reactor either way), to the parity bar where the block solver re-solved in FP64 (its
+    shared-memory atomics order the Jacobian sums differently from launch to launch)."""
     import torch
     _, mech, batch = workload("k53_b4096")
     sub = batch.subset(range(1024))
@@ -290,7 +312,14 @@ def test_autotune_picks_a_shape_with_identical_results(dev):
     assert tuned.precision == base.precision and tuned.ftol == base.ftol
     a = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"], opts=base)
     b = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"], opts=tuned)
-    assert torch.equal(a["Y"], b["Y"]) and torch.equal(a["status"], b["status"])
+    sa, sb = a["status"].cpu().numpy(), b["status"].cpu().numpy()
+    assert np.all(np.isin(sa, psr.CONVERGED_STATES) == np.isin(sb, psr.CONVERGED_STATES))
+    warp = (sa == psr.PSR_CONVERGED) & (sb == psr.PSR_CONVERGED)
+    assert warp.mean() >= 0.95
+    assert torch.equal(a["Y"][torch.from_numpy(warp).to(dev)], b["Y"][torch.from_numpy(warp).to(dev)])
+    Ya, Yb = a["Y"].cpu().numpy(), b["Y"].cpu().numpy()
+    big = Ya > Y_MIN
+    assert np.max(np.where(big, np.abs(Yb - Ya) / np.where(big, Ya, 1.0), 0.0)) <= Y_REL
     with pytest.raises(psr.PsrError):
         psr.autotune(gm, t["Y_in"][:0], t["T_in"][:0], t["tau"][:0], t["P"][:0], t["Y0"][:0], t["T0"][:0])
 
