@@ -39,7 +39,7 @@ FP64_PEAK_TFLOPS = 1.25          # nominal GB300 FP64 (non-tensor) rate
 EXP_FLOPS, LOG_FLOPS, DIV_FLOPS = 40.0, 73.0, 16.0
 # dram__bytes_read + write of one mixed-form launch on k53_b4096, from the ncu capture of
 # the current solver build (to be re-measured whenever the kernel changes)
-K53_TRAFFIC_BYTES = 4336896
+K53_TRAFFIC_BYTES = 5050112
 
 
 def parse():
