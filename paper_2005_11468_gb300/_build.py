@@ -11,6 +11,10 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpsr.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["psr_solve.cu", "psr_block.cu", "mech.cpp"]
+# psr_solve_inst.cu is built once per solve_kernel instantiation (Jacobian precision,
+# soot, finite-difference Jacobian): six objects that compile in parallel.
+INSTANCES = [(tj, soot, fdj) for soot, fdj in ((0, 0), (0, 1), (1, 0)) for tj in ("float", "double")]
+HEADERS = ["psr_internal.h", "psr_device.cuh", "psr_warp.cuh"]
 
 
 def _nvcc():
@@ -20,9 +24,10 @@ def _nvcc():
     return exe
 
 
-def _compile(src, nvcc):
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-    cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
+def _compile(unit, nvcc):
+    src, defines, tag = unit
+    obj = os.path.join(BUILD, os.path.basename(src) + tag + ".o")
+    cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", *defines,
            f"-I{INCLUDE}", f"-I{CSRC}", "-c", os.path.join(CSRC, src), "-o", obj]
     if src.endswith(".cpp"):
         cmd.insert(1, "-x")
@@ -33,16 +38,21 @@ def _compile(src, nvcc):
 
 def build(force=False):
     """Compile every translation unit and link libpsr.so; returns the library path."""
-    srcs = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, "psr_internal.h"), os.path.join(CSRC, "psr_device.cuh"),
-                                                         os.path.join(INCLUDE, "psr.h")]
+    srcs = ([os.path.join(CSRC, s) for s in SOURCES + ["psr_solve_inst.cu"] + HEADERS]
+            + [os.path.join(INCLUDE, "psr.h")])
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(s) <= t for s in srcs) and os.path.getmtime(__file__) <= t:
             return LIB
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    with concurrent.futures.ThreadPoolExecutor(len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, nvcc), SOURCES))
+    units = [(s, [], "") for s in SOURCES]
+    units += [("psr_solve_inst.cu", [f"-DPSR_INST_TJ={tj}", f"-DPSR_INST_SOOT={soot}", f"-DPSR_INST_FDJ={fdj}"],
+               f".{tj}{soot}{fdj}") for tj, soot, fdj in INSTANCES]
+    # the slowest units first, so that they start before the small ones take the cores
+    units.sort(key=lambda u: 0 if u[0] == "psr_solve_inst.cu" else 1)
+    with concurrent.futures.ThreadPoolExecutor(min(len(units), max(2, os.cpu_count() or 2))) as ex:
+        objs = list(ex.map(lambda u: _compile(u, nvcc), units))
     tmp = LIB + ".tmp"
     subprocess.run([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs], check=True)
     os.replace(tmp, LIB)
