@@ -1,0 +1,156 @@
+"""The oracle's pins catch plausible mistakes: each case below plants one mistake in the
+oracle (on the CPU, by wrapping one of its functions for the duration of the test) and
+checks that the pins named beside it fail. A mistake no pin caught would be a mistake
+the oracle could carry into every parity verdict unseen.
+
+The mistakes are the kinds the pins were chosen against: a dropped term or factor, a
+wrong sign, a wrong operand, a missing pivot search.
+"""
+import numpy as np
+import pytest
+
+from oracle import psr_oracle as O
+from tests import test_oracle_pins as pins
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+_orig = {name: getattr(O, name) for name in (
+    "equilibrium_constants", "forward_rate_constants", "rates_of_progress", "third_body_concentrations",
+    "troe_broadening", "net_production_rates", "species_thermo", "mixture_state", "gas_residual", "lu_factor")}
+
+
+# ---------------------------------------------------------------- planted mistakes
+def kc_without_pressure_factor(mech, T):
+    """K_c = K_p: the (P_atm / RT)^(sum nu) factor of Eq. (8) dropped."""
+    T = np.asarray(T)
+    return _orig["equilibrium_constants"](mech, T) / (O.P_ATM / (O.R_U * T[:, None])) ** mech.nu.sum(0)[None]
+
+
+def kc_enthalpy_sign(mech, T):
+    """K_p = exp(sum nu S/R + sum nu H/RT): the sign of the enthalpy term of Eq. (9) flipped."""
+    _, h_RT, _ = _orig["species_thermo"](mech, np.asarray(T))
+    return _orig["equilibrium_constants"](mech, T) * np.exp(2.0 * (h_RT @ mech.nu))
+
+
+def kf_activation_sign(mech, T):
+    """k_f = A T^beta exp(+E/RT): the sign of the exponent of Eq. (6) flipped."""
+    T = np.asarray(T)
+    return _orig["forward_rate_constants"](mech, T) * np.exp(2.0 * mech.theta[None] / T[:, None])
+
+
+def q_without_third_body(mech, T, C, lnmult=None):
+    """Third-body rows not multiplied by [M]."""
+    q = _orig["rates_of_progress"](mech, T, C, lnmult)
+    M = _orig["third_body_concentrations"](mech, C)
+    return np.where(mech.is_tb[None], q / M, q)
+
+
+def q_falloff_times_m(mech, T, C, lnmult=None):
+    """Falloff rows multiplied by [M] as well (the Lindemann form already holds it)."""
+    q = _orig["rates_of_progress"](mech, T, C, lnmult)
+    M = _orig["third_body_concentrations"](mech, C)
+    return np.where(mech.is_troe[None], q * M, q)
+
+
+def m_without_efficiencies(mech, C):
+    """[M] = sum_k [X_k]: the collision efficiencies ignored."""
+    return np.repeat(C.sum(axis=1, keepdims=True), mech.I, axis=1)
+
+
+def troe_without_broadening(mech, T, Pr):
+    """F = 1: the Troe broadening factor left out of the falloff rate."""
+    return np.ones_like(np.asarray(Pr))
+
+
+def wdot_sign(mech, q):
+    """wdot = sum nu' q (reactant minus product): the sign of nu in Eq. (4) flipped."""
+    return -_orig["net_production_rates"](mech, q)
+
+
+def wdot_reactants_only(mech, q):
+    """wdot = -sum nu' q: the products' coefficients nu'' left out of nu in Eq. (4)."""
+    return -(q @ mech.nu_f.T)
+
+
+def entropy_without_log_term(mech, T):
+    """S/R without the a1 ln T term of the NASA-7 entropy."""
+    cp, h, s = _orig["species_thermo"](mech, T)
+    T = np.asarray(T)[:, None]
+    a1 = np.where((np.real(T) < mech.t_mid[None, :]), mech.nasa_low[None, :, 0], mech.nasa_high[None, :, 0])
+    return cp, h, s - a1 * np.log(T)
+
+
+def density_without_mean_weight(mech, Y, T, P):
+    """rho = P / (R T): the mean molecular weight left out of the ideal-gas density."""
+    Wbar, rho, C = _orig["mixture_state"](mech, Y, T, P)
+    return Wbar, rho / Wbar, C / Wbar[:, None]
+
+
+def energy_without_inlet_enthalpy(mech, X, inlet, energy="adiabatic", lnmult=None):
+    """Energy row without the inlet term sum_k Y_k,in (h_k(T) - h_k(T_in)) of Eq. (3)."""
+    F = _orig["gas_residual"](mech, X, inlet, energy, lnmult)
+    if energy == "fixed":
+        return F
+    X = np.atleast_2d(X)
+    Y, T = X[:, :mech.K], X[:, mech.K]
+    cp_R, h_RT, _ = _orig["species_thermo"](mech, T)
+    _, h_RT_in, _ = _orig["species_thermo"](mech, np.array([inlet.T_in]))
+    h = h_RT * O.R_U * T[:, None] / mech.W[None]
+    h_in = h_RT_in * O.R_U * inlet.T_in / mech.W[None]
+    cp = np.sum(Y * cp_R * O.R_U / mech.W[None], axis=1)
+    F = F.copy()
+    F[:, mech.K] -= np.sum(inlet.Y_in[None] * (h - h_in), axis=1) / (cp * T)
+    return F
+
+
+def lu_without_pivoting(A):
+    """Doolittle LU with no row interchanges."""
+    A = np.array(A, dtype=np.float64, copy=True)
+    n = A.shape[0]
+    for k in range(n):
+        if A[k, k] == 0 or not np.isfinite(A[k, k]):
+            return A, np.arange(n), False
+        A[k + 1:, k] /= A[k, k]
+        A[k + 1:, k + 1:] -= np.outer(A[k + 1:, k], A[k, k + 1:])
+    return A, np.arange(n), True
+
+
+# ---------------------------------------------------------------- the pins that must fail
+def _call(name, *args):
+    return lambda: getattr(pins, name)(*args)
+
+
+CASES = [
+    ("equilibrium_constants", kc_without_pressure_factor,
+     [_call("test_dimerisation_closed_form"), _call("test_van_t_hoff")]),
+    ("equilibrium_constants", kc_enthalpy_sign,
+     [_call("test_isomerisation_closed_form"), _call("test_van_t_hoff"),
+      _call("test_tau_to_infinity_is_gibbs_equilibrium")]),
+    ("forward_rate_constants", kf_activation_sign, [_call("test_arrhenius_special_cases")]),
+    ("rates_of_progress", q_without_third_body, [_call("test_third_body_isomerisation_closed_form")]),
+    ("rates_of_progress", q_falloff_times_m, [_call("test_falloff_isomerisation_at_the_troe_centre")]),
+    ("third_body_concentrations", m_without_efficiencies,
+     [_call("test_third_body_isomerisation_closed_form"), _call("test_falloff_isomerisation_at_the_troe_centre")]),
+    ("troe_broadening", troe_without_broadening,
+     [_call("test_falloff_isomerisation_at_the_troe_centre"), _call("test_troe_centre_and_limits")]),
+    ("net_production_rates", wdot_sign, [_call("test_isomerisation_closed_form"),
+                                         _call("test_dimerisation_closed_form")]),
+    ("net_production_rates", wdot_reactants_only, [_call("test_wdot_conserves_mass_and_elements", "k10_b64")]),
+    ("species_thermo", entropy_without_log_term, [_call("test_nasa_enthalpy_and_entropy_derivatives", False)]),
+    ("mixture_state", density_without_mean_weight, [_call("test_dimerisation_closed_form")]),
+    ("gas_residual", energy_without_inlet_enthalpy, [_call("test_residual_identities", "k10_b64"),
+                                                     _call("test_newton_finds_only_true_roots_adiabatic_s_curve")]),
+    ("lu_factor", lu_without_pivoting, [_call("test_lu_matches_lapack", 11)]),
+]
+
+
+@pytest.mark.parametrize("target,mistake,catchers", CASES, ids=[c[1].__name__ for c in CASES])
+def test_pins_catch_the_planted_mistake(monkeypatch, target, mistake, catchers):
+    # every named pin passes on the oracle as it is ...
+    for pin in catchers:
+        pin()
+    # ... and fails once the mistake is planted
+    monkeypatch.setattr(O, target, mistake)
+    for pin in catchers:
+        with pytest.raises(AssertionError):
+            pin()

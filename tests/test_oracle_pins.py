@@ -140,6 +140,66 @@ def test_dimerisation_closed_form():
     np.testing.assert_allclose(r.x[1], yA, rtol=1e-10)
 
 
+def _isomer_constants(mech, T, P, Y_in):
+    """rho, W_A and the mass fraction sum S of the A/B pair of the isomerisation goldens
+    (W_A = W_B, so both stay constant at fixed T and P)."""
+    W = mech.comp @ np.array([12.011, 1.008, 15.999, 14.007])
+    S = Y_in[1] + Y_in[2]
+    rho = P / (O.R_U * T) / (Y_in[0] / W[0] + S / W[1])
+    return rho, W, S
+
+
+def test_third_body_isomerisation_closed_form():
+    """A + M <=> B + M with distinct efficiencies, fixed T: the steady balance of A is a
+    quadratic in Y_A (golden file). Catches a dropped [M] factor, efficiencies of the
+    wrong species or default efficiencies where the file lists others."""
+    mech = golden("tb_isomer.psrmech")
+    T, tau, P = 1500.0, 1e-3, synth.ONE_ATM
+    Y_in = np.array([0.5, 0.4, 0.1])
+    inlet = O.Inlet(Y_in, 500.0, tau, P, T_spec=T)
+    r = O.solve_reactor(mech, inlet, np.r_[Y_in, T], energy="fixed")
+    assert r.status == O.CONVERGED
+    rho, W, S = _isomer_constants(mech, T, P, Y_in)
+    kf = 1.0e8
+    kr = kf / math.exp((5.5 - 6.0) - (1500.0 - 2000.0) / T)
+    m0 = 2.5 * rho * Y_in[0] / W[0] + 1.5 * rho * S / W[1]
+    m1 = (0.5 - 1.5) * rho / W[1]
+    a = tau * m1 * (kf + kr)
+    b = 1.0 + tau * m0 * (kf + kr) - tau * m1 * kr * S
+    c = -(Y_in[1] + tau * m0 * kr * S)
+    roots = np.roots([a, b, c]).real
+    YA = roots[(roots >= 0) & (roots <= S)]
+    assert YA.size == 1
+    # the [M] factor matters here: tau k_f [M] is of order one
+    assert 0.1 < tau * kf * (m0 + m1 * YA[0]) < 10
+    np.testing.assert_allclose(r.x[1], YA[0], rtol=1e-12)
+    np.testing.assert_allclose(r.x[2], S - YA[0], rtol=1e-12)
+
+
+def test_falloff_isomerisation_at_the_troe_centre():
+    """A (+M) <=> B (+M), Troe falloff at the centre of the broadening curve (F = F_cent
+    = 1/2, golden file): k_f = k_inf P_r / (1 + P_r) / 2 with P_r = k_0 [M] / k_inf, then
+    the linear isomerisation closed form. Catches a missing Lindemann blend, a missing F,
+    [M] without efficiencies, and an extra [M] factor on a falloff rate of progress."""
+    mech = golden("troe_isomer.psrmech")
+    T, tau, P = 1500.0, 1e-3, synth.ONE_ATM
+    Y_in = np.array([0.5, 0.4, 0.1])
+    inlet = O.Inlet(Y_in, 500.0, tau, P, T_spec=T)
+    r = O.solve_reactor(mech, inlet, np.r_[Y_in, T], energy="fixed")
+    assert r.status == O.CONVERGED
+    rho, W, S = _isomer_constants(mech, T, P, Y_in)
+    k_inf, k_0 = 2000.0, 257582561.28170544
+    M = 2.0 * rho * Y_in[0] / W[0] + rho * S / W[1]
+    Pr = k_0 * M / k_inf
+    # the fixture sits at the centre: log10 P_r + c = 0 with c = -0.4 - 0.67 log10(1/2)
+    assert abs(math.log10(Pr) - 0.4 - 0.67 * math.log10(0.5)) < 1e-9
+    kf = k_inf * Pr / (1.0 + Pr) * 0.5
+    kr = kf / math.exp((5.5 - 6.0) - (1500.0 - 2000.0) / T)
+    YA = (Y_in[1] + tau * kr * S) / (1.0 + tau * (kf + kr))
+    np.testing.assert_allclose(r.x[1], YA, rtol=1e-12)
+    np.testing.assert_allclose(r.x[2], S - YA, rtol=1e-12)
+
+
 # ------------------------------------------------------------------ Troe falloff
 def _troe(alpha, T3, T1, T2):
     return types.SimpleNamespace(troe=np.array([[alpha, T3, T1, T2]]))
