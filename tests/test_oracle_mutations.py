@@ -6,17 +6,24 @@ the oracle could carry into every parity verdict unseen.
 The mistakes are the kinds the pins were chosen against: a dropped term or factor, a
 wrong sign, a wrong operand, a missing pivot search.
 """
+import math
+
 import numpy as np
 import pytest
 
+from oracle import momic_oracle as S
 from oracle import psr_oracle as O
+from tests import test_oracle_adjoint as adjoint_pins
+from tests import test_oracle_momic as momic_pins
 from tests import test_oracle_pins as pins
 
 pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
 
 _orig = {name: getattr(O, name) for name in (
     "equilibrium_constants", "forward_rate_constants", "rates_of_progress", "third_body_concentrations",
-    "troe_broadening", "net_production_rates", "species_thermo", "mixture_state", "gas_residual", "lu_factor")}
+    "troe_broadening", "net_production_rates", "species_thermo", "mixture_state", "gas_residual", "lu_factor",
+    "sensitivities")}
+_orig_soot = {name: getattr(S, name) for name in ("fractional_moment", "soot_sources", "f_half", "grid_f")}
 
 
 # ---------------------------------------------------------------- planted mistakes
@@ -115,9 +122,56 @@ def lu_without_pivoting(A):
     return A, np.arange(n), True
 
 
+def moment_interpolation_linear(logmu, p):
+    """log mu_p interpolated linearly between the neighbouring integer moments (and
+    extrapolated linearly from r = 0, 1 below zero) instead of by the Lagrange polynomials."""
+    lo = int(min(max(math.floor(p), 0), 4))
+    t = p - lo
+    return 10.0 ** ((1 - t) * logmu[..., lo] + t * logmu[..., lo + 1])
+
+
+def coagulation_sign(soot, M, CP, T):
+    """Coagulation sources with the wrong sign (G_0 > 0: coagulation creating particles)."""
+    R, W, G, s = _orig_soot["soot_sources"](soot, M, CP, T)
+    return R, W, -G, s
+
+
+def soot_without_gas_sink(soot, M, CP, T):
+    """Nucleation and growth take no precursor out of the gas."""
+    R, W, G, s = _orig_soot["soot_sources"](soot, M, CP, T)
+    return R, W, G, 0.0 * s
+
+
+def nucleation_without_size(soot, M, CP, T):
+    """Nuclei added to every moment as C_min, not C_min^r."""
+    R, W, G, s = _orig_soot["soot_sources"](soot, M, CP, T)
+    return np.broadcast_to(R[..., 1:2], R.shape).copy(), W, G, s
+
+
+def growth_per_particle(soot, M, CP, T):
+    """Surface growth per particle: the M_0 factor of the total surface left out."""
+    R, W, G, s = _orig_soot["soot_sources"](soot, M, CP, T)
+    return R, W / np.asarray(M)[..., :1], G, s
+
+
+def coagulation_grid_linear(logmu, x, y):
+    """f(1/2) interpolated in f(l) rather than in log f(l)."""
+    w = S.lagrange_weights(range(4), 0.5)
+    return sum(w[l] * _orig_soot["grid_f"](logmu, l, x, y) for l in range(4))
+
+
+def sensitivity_sign(mech, inlet, x, energy="adiabatic", lnmult=None):
+    """S = +J^-1 dF/dp: the minus sign of the implicit-function theorem dropped."""
+    return -_orig["sensitivities"](mech, inlet, x, energy, lnmult)
+
+
 # ---------------------------------------------------------------- the pins that must fail
-def _call(name, *args):
-    return lambda: getattr(pins, name)(*args)
+def _call(name, *args, module=pins):
+    return lambda: getattr(module, name)(*args)
+
+
+def _momic(name):
+    return _call(name, module=momic_pins)
 
 
 CASES = [
@@ -141,16 +195,30 @@ CASES = [
     ("gas_residual", energy_without_inlet_enthalpy, [_call("test_residual_identities", "k10_b64"),
                                                      _call("test_newton_finds_only_true_roots_adiabatic_s_curve")]),
     ("lu_factor", lu_without_pivoting, [_call("test_lu_matches_lapack", 11)]),
+    ("sensitivities", sensitivity_sign,
+     [_call("test_isomerisation_sensitivity_closed_form", module=adjoint_pins),
+      _call("test_sensitivities_match_finite_differences_of_resolved_roots", module=adjoint_pins)]),
+]
+# MOMIC soot (wrapped in oracle/momic_oracle.py)
+SOOT_CASES = [
+    ("fractional_moment", moment_interpolation_linear, [_momic("test_lognormal_interpolation_is_exact")]),
+    ("soot_sources", coagulation_sign, [_momic("test_monodisperse_coagulation_and_growth_closed_forms"),
+                                        _momic("test_coagulation_conserves_carbon_and_reduces_number")]),
+    ("soot_sources", soot_without_gas_sink, [_momic("test_carbon_conservation_gas_plus_soot")]),
+    ("soot_sources", nucleation_without_size, [_momic("test_nucleation_only_steady_state")]),
+    ("soot_sources", growth_per_particle, [_momic("test_monodisperse_coagulation_and_growth_closed_forms")]),
+    ("f_half", coagulation_grid_linear, [_momic("test_monodisperse_coagulation_and_growth_closed_forms")]),
 ]
 
 
-@pytest.mark.parametrize("target,mistake,catchers", CASES, ids=[c[1].__name__ for c in CASES])
-def test_pins_catch_the_planted_mistake(monkeypatch, target, mistake, catchers):
-    # every named pin passes on the oracle as it is ...
-    for pin in catchers:
-        pin()
-    # ... and fails once the mistake is planted
-    monkeypatch.setattr(O, target, mistake)
+ALL = [(O, *c) for c in CASES] + [(S, *c) for c in SOOT_CASES]
+
+
+# The named pins pass on the oracle as it is (their own modules run them unmodified);
+# each must fail once the mistake is planted.
+@pytest.mark.parametrize("module,target,mistake,catchers", ALL, ids=[c[2].__name__ for c in ALL])
+def test_pins_catch_the_planted_mistake(monkeypatch, module, target, mistake, catchers):
+    monkeypatch.setattr(module, target, mistake)
     for pin in catchers:
         with pytest.raises(AssertionError):
             pin()
