@@ -348,6 +348,8 @@ class Options:
     t_min: float = 200.0
     t_max: float = 5000.0
     fd_rel: float = 1e-6        # central-difference step h_j = fd_rel * max(|x_j|, s_j)
+    jacobian: str = "cs"        # Newton's Jacobian: "cs" complex step, "fd" central
+                                #   differences (the paper's choice, Sec. 1)
 
 
 @dataclasses.dataclass
@@ -440,6 +442,16 @@ def jacobian_cs(system, x, h=1e-30):
     return (system.F(X).imag / h).T
 
 
+def newton_jacobian(system, x, opts: Options):
+    """The Jacobian Newton uses: complex step (default) or the paper's central
+    finite differences (Sec. 1), per opts.jacobian. Both reach the same roots."""
+    if opts.jacobian == "fd":
+        return jacobian_fd(system, x, opts)
+    if opts.jacobian != "cs":
+        raise ValueError(f"unknown Jacobian option {opts.jacobian!r}")
+    return jacobian_cs(system, x)
+
+
 def _damped_newton(system, x, c, x_ref, max_it, opts, steady, counter, fnorm=None):
     """Damped Newton on R(y) = F(y) + c (y - x_ref) from y = x (c = 0: the steady
     problem; c = tau/dt D^-1: one backward-Euler step of dx/dt = -D F / tau).
@@ -469,7 +481,7 @@ def _damped_newton(system, x, c, x_ref, max_it, opts, steady, counter, fnorm=Non
         if counter[0] >= opts.max_newton:
             break
         counter[0] += 1
-        J = jacobian_cs(system, y) + np.diag(c)
+        J = newton_jacobian(system, y, opts) + np.diag(c)
         LU, piv, ok = lu_factor(J)
         if not ok:
             break
@@ -515,7 +527,7 @@ def _linearised_step(system, x, c, opts, counter):
         return x, None, False
     counter[0] += 1
     F = system.F(x)[0]
-    LU, piv, ok = lu_factor(jacobian_cs(system, x) + np.diag(c))
+    LU, piv, ok = lu_factor(newton_jacobian(system, x, opts) + np.diag(c))
     if not ok:
         return x, None, False
     dx = lu_solve(LU, piv, -F)

@@ -388,3 +388,21 @@ def test_newton_finds_only_true_roots_adiabatic_s_curve():
         assert min(d) <= 1e-9
         found.add(int(np.argmin(d)))
     assert {0, 2} <= found
+
+
+# ------------------------------------------------------------------ Sec. 1: finite-difference Jacobian
+@pytest.mark.parametrize("name,n", [("k10_b64", 16), ("k53_b4096", 3)])
+def test_fd_jacobian_newton_reaches_the_same_roots(name, n):
+    """Newton steered by the paper's central-difference Jacobian (Sec. 1) converges to
+    the roots the complex-step Jacobian reaches: J only steers the iteration, the root is
+    fixed by the residual."""
+    _, mech, batch = workload(name)
+    cs = O.solve_batch(mech, batch, indices=range(n))
+    fd = O.solve_batch(mech, batch, O.Options(jacobian="fd"), indices=range(n))
+    assert np.all(cs["status"] == O.CONVERGED) and np.all(fd["status"] == O.CONVERGED)
+    assert np.all(np.abs(fd["T"] - cs["T"]) <= 1e-8)
+    big = cs["Y"] > 1e-10
+    rel = np.abs(fd["Y"] - cs["Y"])[big] / cs["Y"][big]
+    assert np.max(rel) <= 1e-6
+    with pytest.raises(ValueError):
+        O.solve_batch(mech, batch, O.Options(jacobian="exact"), indices=range(1))
