@@ -195,6 +195,33 @@ def oracle_time_mixed(per_class):
     return conv_frac / t_avg, "; ".join(detail)
 
 
+def workload_config(name, world, B=None, spec=None):
+    """The `config` object of a workload's JSON line; both arms print the same one (the
+    reference arm's sample is described in its cpu_baseline)."""
+    from paper_2005_11468_gb300 import synth
+    dp = f"dp{world} (independent reactors)"
+    flushed = "flushed (256 MB write) between timed steps"
+    if name == RATES:
+        spec = spec if spec is not None else synth.workload_mechanism(RATES)
+        B = 1000000 if B is None else B
+        return {"workload": f"{RATES}: K={spec.K}, I={spec.I} ({spec.n_tb} third-body, {spec.n_troe} Troe), "
+                            f"B={B} states at T=1800 K, outputs q and wdot",
+                "l2": flushed}
+    if name == MIXED:
+        B = synth.MIXED_WORKLOAD["B"] if B is None else B
+        return {"workload": f"{MIXED}: {B} reactors per GPU, 50/35/15 % of K=10/53/200 mechanisms "
+                            f"(I=24/325/1500), shuffled, one psr_batch_solve_multi call replayed as a CUDA graph",
+                "global_batch": B * world, "precision": "mixed", "parallelism": dp, "l2": flushed}
+    spec = spec if spec is not None else synth.workload_mechanism(name)
+    B = synth.WORKLOADS[name]["B"] if B is None else B
+    if spec.soot is not None:
+        return {"workload": f"{name}: K={spec.K} + 6 MOMIC moments, I={spec.I}, B={B}",
+                "global_batch": B * world, "precision": "mixed", "l2": "flushed between timed steps"}
+    return {"workload": f"{name}: K={spec.K} species, I={spec.I} reactions "
+                        f"({spec.n_tb} third-body, {spec.n_troe} Troe), B={B} reactors per GPU, adiabatic, 1 atm",
+            "global_batch": B * world, "precision": "mixed", "parallelism": dp, "l2": flushed}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -207,7 +234,7 @@ def run_reference(args):
         print(json.dumps({"impl": "reference", "metric": RATES_METRIC, "value": v, "unit": "states/s",
                           "n_gpus": args.gpus, "steps": K, "warmup": W, "ms_per_step": 1e3 * tc * 20000,
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                          "data": "synthetic", "config": {"workload": f"{RATES} (20000 states, vectorised oracle)"},
+                          "data": "synthetic", "config": workload_config(RATES, world),
                           "cpu_baseline": {"value": v, "unit": "states/s", "cores": 1, "kind": "oracle",
                                            "sample": "20000 states"},
                           "e2e": {"value": v, "unit": "states/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
@@ -217,7 +244,7 @@ def run_reference(args):
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": K, "warmup": W, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": f"{MIXED} (class-weighted oracle sample)"},
+                "config": workload_config(MIXED, world),
                 "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": detail},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -232,7 +259,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": K, "warmup": W, "ms_per_step": 1e3 * t_total / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload} (one reactor of the batch per step)"},
+            "config": workload_config(args.workload, world),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"reactors 0..{W + K - 1} of {args.workload}, one per step, "
                                        f"timed steps {W}..{W + K - 1}"},
@@ -362,11 +389,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": avg_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64 residual / f32 Jacobian+LU", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: K={spec.K} species, I={spec.I} reactions "
-                               f"({spec.n_tb} third-body, {spec.n_troe} Troe), B={B} reactors per GPU, "
-                               f"adiabatic, 1 atm",
-                   "global_batch": B * world, "precision": "mixed", "parallelism": f"dp{world} (independent reactors)",
-                   "l2": "flushed (256 MB write) between timed steps"},
+        "config": workload_config(args.workload, world, B, spec),
         "fp64_form": {"value": value64, "unit": UNIT, "ms_per_step": fp64["total_ms"] / len(fp64["ms"]),
                       "converged": fp64["conv"], "roofline_frac": achieved64 / FP64_PEAK_TFLOPS},
         "mixed_vs_fp64": value / value64 if value64 > 0 else None,
@@ -427,8 +450,7 @@ def run_soot_tail(args, spec, batch, mixed, fp64, t, solve, flush, barrier, pg, 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": mixed["total_ms"] / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 residual / f32 Jacobian+LU", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: K={spec.K} + 6 MOMIC moments, I={spec.I}, B={B}",
-                       "global_batch": B * world, "precision": "mixed", "l2": "flushed between timed steps"},
+            "config": workload_config(args.workload, world, B, spec),
             "fp64_form": {"value": value64, "unit": UNIT, "ms_per_step": fp64["total_ms"] / len(fp64["ms"]),
                           "converged": fp64["conv"]},
             "mixed_vs_fp64": value / value64 if value64 > 0 else None,
@@ -573,10 +595,7 @@ def run_multi(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64 residual / f32 Jacobian+LU", "data": "synthetic",
-        "config": {"workload": f"{MIXED}: {B} reactors per GPU, 50/35/15 % of K=10/53/200 mechanisms "
-                               f"(I=24/325/1500), shuffled, one psr_batch_solve_multi call replayed as a CUDA graph",
-                   "global_batch": B * world, "precision": "mixed", "parallelism": f"dp{world} (independent reactors)",
-                   "l2": "flushed (256 MB write) between timed steps"},
+        "config": workload_config(MIXED, world, B),
         "fp64_form": {"value": value64, "unit": UNIT, "ms_per_step": ms64, "converged": int(conv64)},
         "mixed_vs_fp64": value / value64 if value64 > 0 else None,
         "converged_fraction": conv / B,
@@ -689,9 +708,7 @@ def run_rates(args):
     line = {"metric": RATES_METRIC, "value": value, "unit": "states/s", "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms_big, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{RATES}: K={spec.K}, I={spec.I} ({spec.n_tb} third-body, {spec.n_troe} Troe), "
-                                   f"B={B_big} states at T=1800 K, outputs q and wdot",
-                       "l2": "flushed (256 MB write) between timed steps"},
+            "config": workload_config(RATES, world, B_big, spec),
             "states_per_s_by_batch": {str(b): v for b, v in per_b.items()},
             "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
