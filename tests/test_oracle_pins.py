@@ -236,7 +236,7 @@ def test_troe_centre_and_limits():
 
 
 # ------------------------------------------------------------------ Eq. (4): conservation
-@pytest.mark.parametrize("name", ["k10_b64", "k53_b4096"])
+@pytest.mark.parametrize("name", ["k10_b64", "k53_b4096", "k200_b2048", "k53soot_b16384"])
 def test_wdot_conserves_mass_and_elements(name):
     _, mech, _ = workload(name)
     X = random_states(mech, 16, seed=3)
@@ -251,7 +251,7 @@ def test_wdot_conserves_mass_and_elements(name):
     assert np.all(np.abs(elem) <= 1e-13 * (gross @ mech.comp) + 1e-300)
 
 
-@pytest.mark.parametrize("name", ["k10_b64", "k53_b4096"])
+@pytest.mark.parametrize("name", ["k10_b64", "k53_b4096", "k200_b2048", "k53soot_b16384"])
 def test_residual_identities(name):
     """For any state: sum_k F_k = sum_k (Y_k - Y_k,in); the element combinations of F
     equal those of Y - Y_in; and the energy row obeys
