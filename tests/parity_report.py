@@ -171,6 +171,10 @@ def cpu_phase(path, procs):
     d = dict(np.load(path))
     keys = sorted({k.rsplit("|", 2)[0] for k in d})
     tasks = sorted({(k, int(b)) for k in keys for b in d[f"{k}|mixed|idx"]})
+    # one BLAS thread per worker: with a thread pool in each of several processes the
+    # oracle's small matrix products ran 20x slower (oversubscribed cores)
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
     t0 = time.time()
     with mp.get_context("spawn").Pool(procs) as pool:
         res = {(k, b): (x, s, M, c) for k, b, x, s, M, c in pool.imap_unordered(_oracle_task, tasks)}
