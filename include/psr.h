@@ -155,8 +155,9 @@ int psr_batch_solve(const psr_mech *m, int64_t B,
  * scratch, its work-queue counter, sits in a static 256-byte device array that every
  * GPU loading the library keeps until exit. Arguments, outputs and results are those
  * of psr_batch_solve, except that PSR_MIXED runs the single FP32-Jacobian launch (no
- * FP64 fallback, mixed_fallback is ignored); B must not exceed 2^31 - 2^22 (PSR_E_ARG
- * otherwise). The first
+ * FP64 fallback, mixed_fallback is ignored) and the Jacobian is always the analytic one
+ * (options.jacobian is ignored); B must not exceed 2^31 - 2^22 (PSR_E_ARG otherwise).
+ * The first
  * call on each device looks up the array's device address (cudaGetSymbolAddress), so
  * make that first call before any stream capture. All calls share the array: it is
  * zeroed on the stream before each launch, and calls that overlap on the GPU (other
