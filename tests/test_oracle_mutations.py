@@ -1,7 +1,7 @@
 """The oracle's pins catch plausible mistakes: each case below plants one mistake in the
 oracle (on the CPU, by wrapping one of its functions for the duration of the test) and
 checks that the pins named beside it fail. A mistake no pin caught would be a mistake
-the oracle could carry into every parity verdict unseen.
+the oracle could carry into every parity comparison unseen.
 
 The mistakes are the kinds the pins were chosen against: a dropped term or factor, a
 wrong sign, a wrong operand, a missing pivot search.
