@@ -138,9 +138,13 @@ void psr_options_default(psr_options *o);
  * device; no host synchronisation); their counters add up and a success reports
  * PSR_REFINE_FALLBACK. If Y0/T0 alias Y_out/T_out, that re-solve starts from the first
  * launch's final iterate.
+ * Mechanisms with K + 1 <= 64 run one warp per reactor; larger ones (K + 1 <= 512) one
+ * thread block per reactor with the same method.
  * Device memory: a few scratch integers (B + 4 for the fallback, B more when status is
  * NULL) are allocated and freed on the stream.
- * Errors: PSR_E_ARG, PSR_E_UNSUPPORTED (K + 1 > 64 for this kernel), PSR_E_CUDA. */
+ * Errors: PSR_E_ARG (including B > 2^31 - 2^22, the work queue's limit, checked before
+ * the mechanism), PSR_E_UNSUPPORTED (K + 1 > 512; the finite-difference Jacobian with
+ * K + 1 > 64), PSR_E_CUDA, PSR_E_OOM. */
 int psr_batch_solve(const psr_mech *m, int64_t B,
                     const double *Y_in, const double *T_in, const double *tau, const double *P,
                     const double *Y0, const double *T0, const double *rate_mult,
@@ -154,10 +158,11 @@ int psr_batch_solve(const psr_mech *m, int64_t B,
  * allocates nothing (no cudaMalloc, cudaMallocAsync or cudaFree): the solver's only
  * scratch, its work-queue counter, sits in a static 256-byte device array that every
  * GPU loading the library keeps until exit. Arguments, outputs and results are those
- * of psr_batch_solve, except that PSR_MIXED runs the single FP32-Jacobian launch (no
- * FP64 fallback, mixed_fallback is ignored) and the Jacobian is always the analytic one
- * (options.jacobian is ignored); B must not exceed 2^31 - 2^22 (PSR_E_ARG otherwise).
- * The first
+ * of psr_batch_solve, with three differences: only mechanisms with K + 1 <= 64 (the
+ * warp-per-reactor solver; larger ones need allocated Jacobian slots) are accepted,
+ * PSR_E_UNSUPPORTED otherwise; PSR_MIXED runs the single FP32-Jacobian launch (no FP64
+ * re-solve of unconverged reactors, mixed_fallback is ignored); and B must not exceed
+ * 2^31 - 2^22 (PSR_E_ARG otherwise). Both Jacobian options are honoured. The first
  * call on each device looks up the array's device address (cudaGetSymbolAddress), so
  * make that first call before any stream capture. All calls share the array: it is
  * zeroed on the stream before each launch, and calls that overlap on the GPU (other

@@ -11,6 +11,10 @@ namespace psr {
 constexpr double kRu = 8.314462618e7;   // erg / (mol K)
 constexpr double kPatm = 1.01325e6;     // dyn / cm^2, standard state of Eq. (8)
 constexpr int kMaxWarpN = 64;           // K + 1 handled by one warp (two rows per lane)
+// Largest batch of the persistent solvers: their int32 work-queue counter ends at B plus one
+// overshooting claim per resident warp (at most 64 warps on each of at most 2^16 SMs), so
+// this headroom keeps it from wrapping.
+constexpr int64_t kMaxBatch = (int64_t(1) << 31) - (int64_t(1) << 22);
 
 enum RxnType : int8_t { kElem = 0, kThirdBody = 1, kTroe = 2 };
 

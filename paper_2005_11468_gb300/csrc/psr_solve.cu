@@ -465,9 +465,6 @@ int launch_eval(const Mech &m, const Batch &bt, int energy, int want_J, double *
 // race on it.
 constexpr int kNoAllocScratchInts = 64;                 // 256 bytes
 static __device__ __align__(256) int32_t g_noalloc_scratch[kNoAllocScratchInts];
-// largest batch whose work-queue counter (int32, overshot by at most one claim per
-// warp of the grid) cannot overflow
-constexpr int64_t kNoAllocMaxB = (int64_t(1) << 31) - (int64_t(1) << 22);
 
 constexpr int kMaxDevices = 64;
 std::atomic<int32_t *> g_noalloc_addr[kMaxDevices];
@@ -491,38 +488,14 @@ int noalloc_scratch(int32_t **out) {
     return PSR_OK;
 }
 
+// The persistent solver with its work-queue counter in the static array (the launcher
+// zeroes it on the stream before the launch).
 template <class TJ>
 int launch_solve_noalloc(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int bps_req, cudaStream_t st) {
     int32_t *queue = nullptr;
-    int rc = noalloc_scratch(&queue);
+    const int rc = noalloc_scratch(&queue);
     if (rc != PSR_OK) return rc;
-    const size_t wsb = ws_bytes<TJ>(m.K, m.I, m.K + 1 + m.dev.nsoot, m.n_troe, m.dev.nsoot);
-    int dev = 0;
-    cudaGetDevice(&dev);
-    int max_smem = 0, nsm = 0;
-    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int wpb = std::min(wpb_req > 0 ? wpb_req : kDefaultSolveWarps, kMaxSolveWarps);
-    while (wpb > 1 && size_t(wpb) * wsb > size_t(max_smem)) --wpb;
-    const size_t smem = size_t(wpb) * wsb;
-    if (smem > size_t(max_smem))
-        return set_error(PSR_E_UNSUPPORTED, "mechanism too large for one warp's shared memory");
-    const void *kern = solve_kernel_entry<TJ, false, false>();
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return cuda_error("cudaFuncSetAttribute", e);
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpb * 32, smem);
-    if (e != cudaSuccess) return cuda_error("occupancy", e);
-    if (per_sm < 1) return set_error(PSR_E_UNSUPPORTED, "solver kernel does not fit on an SM");
-    if (bps_req > 0 && bps_req < per_sm) per_sm = bps_req;
-    int64_t want = (bt.B + wpb - 1) / wpb;
-    int64_t grid = std::min<int64_t>(int64_t(per_sm) * nsm, want);
-    if (grid < 1) grid = 1;
-    e = cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
-    if (e != cudaSuccess) return cuda_error("cudaMemsetAsync(work queue)", e);
-    e = launch_solve_kernel<TJ, false, false>(unsigned(grid), wpb * 32, smem, st, m.dev, bt, o, queue, wsb);
-    if (e != cudaSuccess) return cuda_error("solve_kernel launch", e);
-    return PSR_OK;
+    return launch_solve_q<TJ>(m, bt, o, wpb_req, bps_req, st, queue);
 }
 
 // Mechanisms with at most 64 unknowns run on the warp-per-reactor kernels, larger gas
@@ -594,13 +567,13 @@ int psr_batch_solve(const psr_mech *m, int64_t B, const double *Y_in, const doub
                     const double *P, const double *Y0, const double *T0, const double *rate_mult, double *Y_out,
                     double *T_out, int32_t *iters, int32_t *ts_steps, int32_t *status, double *fnorm,
                     int32_t *nfev, const psr_options *opt, void *cuda_stream) {
+    if (B < 0) return set_error(PSR_E_ARG, "B < 0");
+    if (B > kMaxBatch) return set_error(PSR_E_ARG, "B exceeds the work-queue limit of " + std::to_string(kMaxBatch));
     int rc = check_mech(m);
     if (rc) return rc;
     if (m->m.has_soot)
         return set_error(PSR_E_ARG, "mechanism carries soot: use the _soot entry points");
-    if (B < 0) return set_error(PSR_E_ARG, "B < 0");
     if (B == 0) return PSR_OK;
-    if (B > (int64_t(1) << 31) - 64) return set_error(PSR_E_ARG, "B too large");
     if (!Y_in || !T_in || !tau || !P || !Y0 || !T0 || !Y_out || !T_out)
         return set_error(PSR_E_ARG, "psr_batch_solve: required pointer is NULL");
     if ((rc = check_opts(opt))) return rc;
@@ -623,16 +596,16 @@ int psr_batch_solve_noalloc(const psr_mech *m, int64_t B, const double *Y_in, co
                             const double *P, const double *Y0, const double *T0, const double *rate_mult,
                             double *Y_out, double *T_out, int32_t *iters, int32_t *ts_steps, int32_t *status,
                             double *fnorm, int32_t *nfev, const psr_options *opt, void *cuda_stream) {
+    if (B < 0) return set_error(PSR_E_ARG, "B < 0");
+    if (B > kMaxBatch)
+        return set_error(PSR_E_ARG, "psr_batch_solve_noalloc: B exceeds the static work-queue limit of " +
+                                        std::to_string(kMaxBatch) + " reactors");
     int rc = check_mech(m);
     if (rc) return rc;
     if (m->m.has_soot)
         return set_error(PSR_E_ARG, "mechanism carries soot: use the _soot entry points");
     if (!warp_path(m))
         return set_error(PSR_E_UNSUPPORTED, "psr_batch_solve_noalloc: at most 64 unknowns (K + 1)");
-    if (B < 0) return set_error(PSR_E_ARG, "B < 0");
-    if (B > kNoAllocMaxB)
-        return set_error(PSR_E_ARG, "psr_batch_solve_noalloc: B exceeds the static work-queue limit of " +
-                                        std::to_string(kNoAllocMaxB) + " reactors");
     if (B == 0) return PSR_OK;
     if (!Y_in || !T_in || !tau || !P || !Y0 || !T0 || !Y_out || !T_out)
         return set_error(PSR_E_ARG, "psr_batch_solve_noalloc: required pointer is NULL");
@@ -653,12 +626,12 @@ int psr_batch_solve_soot(const psr_mech *m, int64_t B, const double *Y_in, const
                          const double *rate_mult, double *Y_out, double *T_out, double *M_out, int32_t *iters,
                          int32_t *ts_steps, int32_t *status, double *fnorm, int32_t *nfev, const psr_options *opt,
                          void *cuda_stream) {
+    if (B < 0) return set_error(PSR_E_ARG, "B < 0");
+    if (B > kMaxBatch) return set_error(PSR_E_ARG, "B exceeds the work-queue limit of " + std::to_string(kMaxBatch));
     int rc = check_mech(m);
     if (rc) return rc;
     if (!m->m.has_soot) return set_error(PSR_E_ARG, "mechanism has no soot record: use psr_batch_solve");
-    if (B < 0) return set_error(PSR_E_ARG, "B < 0");
     if (B == 0) return PSR_OK;
-    if (B > (int64_t(1) << 31) - 64) return set_error(PSR_E_ARG, "B too large");
     if (!Y_in || !T_in || !tau || !P || !M_in || !Y0 || !T0 || !Y_out || !T_out || !M_out)
         return set_error(PSR_E_ARG, "psr_batch_solve_soot: required pointer is NULL");
     if ((rc = check_opts(opt))) return rc;
@@ -680,7 +653,7 @@ int psr_eval_residual_soot(const psr_mech *m, int64_t B, const double *Y_in, con
     int rc = check_mech(m);
     if (rc) return rc;
     if (!m->m.has_soot) return set_error(PSR_E_ARG, "mechanism has no soot record");
-    if (B < 0 || (energy != PSR_ADIABATIC && energy != PSR_FIXED_T)) return set_error(PSR_E_ARG, "bad B or energy");
+    if (B < 0 || B > kMaxBatch || (energy != PSR_ADIABATIC && energy != PSR_FIXED_T)) return set_error(PSR_E_ARG, "bad B or energy");
     if (B == 0) return PSR_OK;
     if (!Y_in || !T_in || !tau || !P || !M_in || !Y || !T || !Mom || !F_out) return set_error(PSR_E_ARG, "NULL pointer");
     Batch bt{B, Y_in, T_in, tau, P, Y, T, rate_mult, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
@@ -695,7 +668,7 @@ int psr_eval_jacobian_soot(const psr_mech *m, int64_t B, const double *Y_in, con
     int rc = check_mech(m);
     if (rc) return rc;
     if (!m->m.has_soot) return set_error(PSR_E_ARG, "mechanism has no soot record");
-    if (B < 0 || (energy != PSR_ADIABATIC && energy != PSR_FIXED_T) ||
+    if (B < 0 || B > kMaxBatch || (energy != PSR_ADIABATIC && energy != PSR_FIXED_T) ||
         (precision != PSR_FP64 && precision != PSR_MIXED))
         return set_error(PSR_E_ARG, "bad B, energy or precision");
     if (B == 0) return PSR_OK;
@@ -713,7 +686,7 @@ int psr_batch_solve_host(const psr_mech *m, int64_t B, const double *Y_in, const
                          double *fnorm, int32_t *nfev, const psr_options *opt, void *cuda_stream) {
     int rc = check_mech(m);
     if (rc) return rc;
-    if (B < 0) return set_error(PSR_E_ARG, "B < 0");
+    if (B < 0 || B > kMaxBatch) return set_error(PSR_E_ARG, "B out of range");
     if (B == 0) return PSR_OK;
     if (!Y_in || !T_in || !tau || !P || !Y0 || !T0 || !Y_out || !T_out)
         return set_error(PSR_E_ARG, "psr_batch_solve_host: required pointer is NULL");
@@ -764,7 +737,7 @@ int psr_eval_residual(const psr_mech *m, int64_t B, const double *Y_in, const do
     if (rc) return rc;
     if (m->m.has_soot)
         return set_error(PSR_E_ARG, "mechanism carries soot: use the _soot entry points");
-    if (B < 0 || (energy != PSR_ADIABATIC && energy != PSR_FIXED_T)) return set_error(PSR_E_ARG, "bad B or energy");
+    if (B < 0 || B > kMaxBatch || (energy != PSR_ADIABATIC && energy != PSR_FIXED_T)) return set_error(PSR_E_ARG, "bad B or energy");
     if (B == 0) return PSR_OK;
     if (!Y_in || !T_in || !tau || !P || !Y || !T || !F_out) return set_error(PSR_E_ARG, "NULL pointer");
     Batch bt{B, Y_in, T_in, tau, P, Y, T, rate_mult, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -779,7 +752,7 @@ int psr_eval_jacobian(const psr_mech *m, int64_t B, const double *Y_in, const do
     if (rc) return rc;
     if (m->m.has_soot)
         return set_error(PSR_E_ARG, "mechanism carries soot: use the _soot entry points");
-    if (B < 0 || (energy != PSR_ADIABATIC && energy != PSR_FIXED_T) ||
+    if (B < 0 || B > kMaxBatch || (energy != PSR_ADIABATIC && energy != PSR_FIXED_T) ||
         (precision != PSR_FP64 && precision != PSR_MIXED))
         return set_error(PSR_E_ARG, "bad B, energy or precision");
     if (B == 0) return PSR_OK;
@@ -798,7 +771,7 @@ int psr_batch_adjoint(const psr_mech *m, int64_t B, const double *Y_in, const do
     if (rc) return rc;
     if (m->m.has_soot)
         return set_error(PSR_E_ARG, "mechanism carries soot: use the _soot entry points");
-    if (B < 0 || (energy != PSR_ADIABATIC && energy != PSR_FIXED_T)) return set_error(PSR_E_ARG, "bad B or energy");
+    if (B < 0 || B > kMaxBatch || (energy != PSR_ADIABATIC && energy != PSR_FIXED_T)) return set_error(PSR_E_ARG, "bad B or energy");
     if (B == 0) return PSR_OK;
     if (!Y_in || !T_in || !tau || !P || !Y || !T || !g || !grad_out)
         return set_error(PSR_E_ARG, "psr_batch_adjoint: required pointer is NULL");
@@ -821,7 +794,7 @@ int psr_batch_adjoint(const psr_mech *m, int64_t B, const double *Y_in, const do
 
 int psr_batch_lu_solve(int64_t B, int32_t n, const double *A, const double *r, double *x_out, int32_t *ok_out,
                        int32_t precision, void *cuda_stream) {
-    if (B < 0 || n < 1 || n > 512 || (precision != PSR_FP64 && precision != PSR_MIXED))
+    if (B < 0 || B > kMaxBatch || n < 1 || n > 512 || (precision != PSR_FP64 && precision != PSR_MIXED))
         return set_error(PSR_E_ARG, "psr_batch_lu_solve: bad B, n or precision");
     if (B == 0) return PSR_OK;
     if (!A || !r || !x_out || !ok_out) return set_error(PSR_E_ARG, "psr_batch_lu_solve: NULL pointer");
@@ -852,14 +825,14 @@ int psr_batch_solve_multi(const psr_mech *const *mechs, int32_t n_mech, int64_t 
                           int32_t *iters, int32_t *ts_steps, int32_t *status, double *fnorm, int32_t *nfev,
                           const psr_options *opt, void *cuda_stream) {
     if (!mechs || n_mech < 1 || n_mech > kMaxMechs) return set_error(PSR_E_ARG, "n_mech must be 1..8");
+    if (B < 0) return set_error(PSR_E_ARG, "B < 0");
+    if (B > kMaxBatch) return set_error(PSR_E_ARG, "B exceeds the work-queue limit of " + std::to_string(kMaxBatch));
     for (int c = 0; c < n_mech; ++c) {
         const int rc = check_mech(mechs[c]);
         if (rc) return rc;
         if (mechs[c]->m.has_soot) return set_error(PSR_E_ARG, "psr_batch_solve_multi: gas mechanisms only");
     }
-    if (B < 0) return set_error(PSR_E_ARG, "B < 0");
     if (B == 0) return PSR_OK;
-    if (B > (int64_t(1) << 31) - 64) return set_error(PSR_E_ARG, "B too large");
     if (!mech_id || !row_off || !Y_in || !T_in || !tau || !P || !Y0 || !T0 || !Y_out || !T_out)
         return set_error(PSR_E_ARG, "psr_batch_solve_multi: required pointer is NULL");
     int rc = check_opts(opt);
@@ -996,7 +969,7 @@ int psr_eval_rates(const psr_mech *m, int64_t B, const double *Y, const double *
     int rc = check_mech(m);
     if (rc) return rc;
     if (m->m.has_soot) return set_error(PSR_E_ARG, "psr_eval_rates: gas mechanisms only");
-    if (B < 0) return set_error(PSR_E_ARG, "B < 0");
+    if (B < 0 || B > kMaxBatch) return set_error(PSR_E_ARG, "B out of range");
     if (B == 0) return PSR_OK;
     if (!Y || !T || !P) return set_error(PSR_E_ARG, "psr_eval_rates: NULL state pointer");
     RatesOut ro{kf_out, kr_out, q_out, wdot_out};
@@ -1030,7 +1003,7 @@ int psr_eval_jacobian_fd(const psr_mech *m, int64_t B, const double *Y_in, const
     if (rc) return rc;
     if (m->m.has_soot || !warp_path(m))
         return set_error(PSR_E_UNSUPPORTED, "finite-difference Jacobian: gas mechanisms with K + 1 <= 64");
-    if (B < 0 || (energy != PSR_ADIABATIC && energy != PSR_FIXED_T)) return set_error(PSR_E_ARG, "bad B or energy");
+    if (B < 0 || B > kMaxBatch || (energy != PSR_ADIABATIC && energy != PSR_FIXED_T)) return set_error(PSR_E_ARG, "bad B or energy");
     if (B == 0) return PSR_OK;
     if (!Y_in || !T_in || !tau || !P || !Y || !T || !J_out) return set_error(PSR_E_ARG, "NULL pointer");
     Batch bt{B, Y_in, T_in, tau, P, Y, T, rate_mult, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};

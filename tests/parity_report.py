@@ -22,8 +22,6 @@ component better than about cond * 1e-16 relative); "gpu-unconv" = the GPU did n
 converge. Reactors the oracle did not converge are counted apart.
 """
 import argparse
-import math
-import multiprocessing as mp
 import os
 import sys
 import time
@@ -35,6 +33,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 from paper_2005_11468_gb300 import synth  # noqa: E402
+from tests import oracle_pool  # noqa: E402
 
 Y_REL, Y_MIN, T_ABS, M_REL = 1e-6, 1e-10, 1e-8, 1e-5
 SAMPLE_SEED = 20051146 + 97
@@ -51,7 +50,10 @@ def sample(B, m, salt):
 
 
 # ------------------------------------------------------------------------------ GPU phase
-def gpu_phase(path):
+def gpu_results(samples=SAMPLES, mixed_samples=MIXED_SAMPLES):
+    """Solve each workload's full batch in both forms on cuda:0 through the C ABI and keep
+    the outputs of the seeded sample (the first `samples[name]` of the report's sample, so
+    that a smaller sample is a subset of the larger one). Returns the arrays by key."""
     import torch
     from paper_2005_11468_gb300 import _build, psr
     _build.build()
@@ -61,11 +63,13 @@ def gpu_phase(path):
     def dv(a, dtype=torch.float64):
         return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device=dev)
 
-    for salt, (name, m) in enumerate(SAMPLES.items()):
+    for salt, name in enumerate(SAMPLES):
+        if name not in samples:
+            continue
         spec = synth.workload_mechanism(name)
         gm = psr.Mechanism(synth.mechanism_text(spec))
         batch = synth.workload_batch(name, spec)
-        idx = sample(batch.B, m, salt)
+        idx = sample(batch.B, SAMPLES[name], salt)[:samples[name]]
         t = {k: dv(getattr(batch, k)) for k in ("Y_in", "T_in", "tau", "P", "Y0", "T0")}
         for form, prec in FORMS:
             t0 = time.time()
@@ -88,6 +92,8 @@ def gpu_phase(path):
             print(f"{key}: {time.time() - t0:.1f} s, converged {out[key + '|conv_all'][0]:.4f}", flush=True)
         gm.close()
 
+    if mixed_samples is None:
+        return out
     specs = [synth.workload_mechanism(nm) for nm in synth.MIXED_WORKLOAD["parts"]]
     gms = [psr.Mechanism(synth.mechanism_text(sp)) for sp in specs]
     mb = synth.mixed_batch(specs)
@@ -100,7 +106,7 @@ def gpu_phase(path):
         Y, T, st = r["Y"].cpu().numpy(), r["T"].cpu().numpy(), r["status"].cpu().numpy()
         for c, spec in enumerate(specs):
             mem = mb["members"][c]
-            j = sample(len(mem), MIXED_SAMPLES[c], 50 + c)
+            j = sample(len(mem), MIXED_SAMPLES[c], 50 + c)[:mixed_samples[c]]
             rows = mem[j]
             key = f"mixed_b32768:{synth.MIXED_WORKLOAD['parts'][c]}|{form}"
             out[key + "|idx"] = j
@@ -109,120 +115,89 @@ def gpu_phase(path):
             out[key + "|status"] = st[rows]
             out[key + "|conv_all"] = np.array([np.isin(st[mem], psr.CONVERGED_STATES).mean()])
         print(f"mixed_b32768|{form}: converged {np.isin(st, psr.CONVERGED_STATES).mean():.4f}", flush=True)
-    np.savez(path, **out)
+    for g in gms:
+        g.close()
+    return out
+
+
+def gpu_phase(path):
+    np.savez(path, **gpu_results())
 
 
 # ------------------------------------------------------------------------------ CPU phase
-_CACHE = {}
-
-
-def _problem(key):
-    """Oracle mechanism and batch of a result key (workload or mixed class)."""
-    from oracle import psr_oracle as O
-    if key not in _CACHE:
-        if key.startswith("mixed_b32768:"):
-            part = key.split(":")[1]
-            specs = [synth.workload_mechanism(nm) for nm in synth.MIXED_WORKLOAD["parts"]]
-            c = synth.MIXED_WORKLOAD["parts"].index(part)
-            mb = synth.mixed_batch(specs)
-            spec, batch = specs[c], mb["batches"][c]
-        else:
-            spec = synth.workload_mechanism(key)
-            batch = synth.workload_batch(key, spec)
-        _CACHE[key] = (O.Mechanism(synth.mechanism_text(spec)), batch, spec.soot is not None)
-    return _CACHE[key]
-
-
-def _oracle_task(arg):
-    """One oracle solve; returns the root, its status and the condition number of the
-    oracle's Jacobian there."""
-    from oracle import momic_oracle as S
-    from oracle import psr_oracle as O
-    key, b = arg
-    mech, batch, soot = _problem(key)
-    inlet = O.inlet_of(batch, b)
-    if soot:
-        r, M = S.solve_soot_reactor(mech, inlet, batch.Y0[b], batch.T0[b], batch.M_in[b])
-        system = S.SootSystem(mech, inlet, batch.M_in[b])
-    else:
-        r = O.solve_reactor(mech, inlet, np.r_[batch.Y0[b], batch.T0[b]])
-        M = None
-        system = O.GasSystem(mech, inlet)
-    cond = float(np.linalg.cond(O.jacobian_cs(system, r.x))) if r.status == O.CONVERGED else math.nan
-    return key, int(b), r.x[:mech.K + 1].copy(), int(r.status), M, cond
-
-
-def _gpu_root_residual(key, b, Y, T, M):
-    from oracle import momic_oracle as S
-    from oracle import psr_oracle as O
-    mech, batch, soot = _problem(key)
-    inlet = O.inlet_of(batch, b)
-    if soot:
-        system = S.SootSystem(mech, inlet, batch.M_in[b])
-        x = np.r_[Y, T, np.log(M / system.soot.scale)]
-    else:
-        system = O.GasSystem(mech, inlet)
-        x = np.r_[Y, T]
-    return float(np.max(np.abs(system.F(x[None])[0])))
-
-
-def cpu_phase(path, procs):
-    from oracle import psr_oracle as O
-    d = dict(np.load(path))
+def oracle_tasks(d, want_cond=True):
     keys = sorted({k.rsplit("|", 2)[0] for k in d})
-    tasks = sorted({(k, int(b)) for k in keys for b in d[f"{k}|mixed|idx"]})
-    # one BLAS thread per worker: with a thread pool in each of several processes the
-    # oracle's small matrix products ran 20x slower (oversubscribed cores)
-    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
-        os.environ[var] = "1"
-    t0 = time.time()
-    with mp.get_context("spawn").Pool(procs) as pool:
-        res = {(k, b): (x, s, M, c) for k, b, x, s, M, c in pool.imap_unordered(_oracle_task, tasks)}
-    print(f"oracle: {len(tasks)} reactors in {time.time() - t0:.0f} s on {procs} processes\n")
+    return sorted({(k, int(b), want_cond) for k in keys for b in d[f"{k}|mixed|idx"]})
+
+
+def classify(d, res):
+    """One row per workload and form: counts of pass / other branch / off bar / GPU
+    unconverged / oracle unconverged among the sampled reactors, and the error maxima."""
+    from oracle import psr_oracle as O
     from paper_2005_11468_gb300.psr import CONVERGED_STATES
-    print("| workload | form | sampled | pass | other branch | off bar (max cond J) | GPU unconv. | "
-          "oracle unconv. | max rel err Y (Y>1e-10) | median | max abs err T (K) | max rel err M | "
-          "converged (full batch) |")
-    print("|---|---|---|---|---|---|---|---|---|---|---|---|---|")
+    keys = sorted({k.rsplit("|", 2)[0] for k in d})
+    rows = []
     for key in keys:
-        mech, batch, soot = _problem(key)
+        mech, batch, soot = oracle_pool.problem(key)
         K = mech.K
         for form, _ in FORMS:
             p = f"{key}|{form}"
             idx, Y, T, st = d[p + "|idx"], d[p + "|Y"], d[p + "|T"], d[p + "|status"]
             M = d.get(p + "|M")
-            n_pass = n_branch = n_off = n_gu = n_ou = 0
-            ey, et, em, conds = [], [], [], []
+            row = dict(key=key, form=form, sampled=len(idx), n_pass=0, branch=0, off=0, gpu_unconv=0,
+                       oracle_unconv=0, ey=[], et=[], em=[], conds=[], conv_all=float(d[p + "|conv_all"][0]),
+                       soot=M is not None)
             for j, b in enumerate(idx):
                 x, s, Mo, cond = res[(key, int(b))]
                 if s != O.CONVERGED:
-                    n_ou += 1
+                    row["oracle_unconv"] += 1
                     continue
                 if st[j] not in CONVERGED_STATES:
-                    n_gu += 1
+                    row["gpu_unconv"] += 1
                     continue
                 if abs(T[j] - x[K]) > 1.0:
-                    fr = _gpu_root_residual(key, int(b), Y[j], T[j], None if M is None else M[j])
-                    n_branch += fr <= 1e-7
-                    n_off += fr > 1e-7
+                    fr = oracle_pool.root_residual(key, int(b), Y[j], T[j], None if M is None else M[j])
+                    row["branch" if fr <= 1e-7 else "off"] += 1
                     continue
                 big = x[:K] > Y_MIN
                 rel = float(np.max(np.abs(Y[j][big] - x[:K][big]) / x[:K][big]))
                 dT = float(abs(T[j] - x[K]))
                 rm = float(np.max(np.abs(M[j] - Mo) / Mo)) if M is not None else 0.0
-                ey.append(rel)
-                et.append(dT)
-                em.append(rm)
+                row["ey"].append(rel)
+                row["et"].append(dT)
+                row["em"].append(rm)
                 if rel <= Y_REL and dT <= T_ABS and rm <= M_REL:
-                    n_pass += 1
+                    row["n_pass"] += 1
                 else:
-                    n_off += 1
-                    conds.append(cond)
-            offs = f"{n_off}" + (f" ({max(conds):.1e})" if conds else "")
-            fmt = (lambda v: f"{max(v):.1e}") if ey else (lambda v: "–")
-            print(f"| {key} | {form} | {len(idx)} | {n_pass} | {n_branch} | {offs} | {n_gu} | {n_ou} | "
-                  f"{fmt(ey)} | {np.median(ey) if ey else float('nan'):.1e} | {fmt(et)} | "
-                  f"{fmt(em) if M is not None else '–'} | {d[p + '|conv_all'][0]:.4f} |")
+                    row["off"] += 1
+                    row["conds"].append(cond)
+            rows.append(row)
+    return rows
+
+
+def table(rows):
+    lines = ["| workload | form | sampled | pass | other branch | off bar (max cond J) | GPU unconv. | "
+             "oracle unconv. | max rel err Y (Y>1e-10) | median | max abs err T (K) | max rel err M | "
+             "converged (full batch) |",
+             "|---|---|---|---|---|---|---|---|---|---|---|---|---|"]
+    for r in rows:
+        ey = r["ey"]
+        offs = f"{r['off']}" + (f" ({max(r['conds']):.1e})" if r["conds"] else "")
+        fmt = (lambda v: f"{max(v):.1e}") if ey else (lambda v: "–")
+        lines.append(f"| {r['key']} | {r['form']} | {r['sampled']} | {r['n_pass']} | {r['branch']} | {offs} | "
+                     f"{r['gpu_unconv']} | {r['oracle_unconv']} | {fmt(ey)} | "
+                     f"{np.median(ey) if ey else float('nan'):.1e} | {fmt(r['et'])} | "
+                     f"{fmt(r['em']) if r['soot'] else '–'} | {r['conv_all']:.4f} |")
+    return "\n".join(lines)
+
+
+def cpu_phase(path, procs):
+    d = dict(np.load(path))
+    tasks = oracle_tasks(d)
+    t0 = time.time()
+    res = oracle_pool.solve(tasks, procs)
+    print(f"oracle: {len(tasks)} reactors in {time.time() - t0:.0f} s on {procs} processes\n")
+    print(table(classify(d, res)))
 
 
 def main():

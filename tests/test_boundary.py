@@ -84,3 +84,22 @@ def test_option_defaults_agree(L):
                  "dt_shrink", "y_floor", "t_min", "t_max", "max_newton", "max_damp", "max_ts_rounds",
                  "ts_steps", "ts_newton"):
         assert getattr(o, name) == getattr(c, name), name
+
+
+def test_batch_limit_is_checked_before_anything_else(L):
+    """Persistent solvers take one work-queue ticket per reactor plus one overshoot per
+    resident warp on an int32 counter: batches above 2^31 - 2^22 are refused with
+    PSR_E_ARG before the mechanism or any pointer is looked at."""
+    for B in ((1 << 31) - 64, (1 << 31) - (1 << 22) + 1):
+        assert L.psr_batch_solve(None, B, *([None] * 14), None, None) == -1
+        assert "work-queue limit" in L.psr_last_error().decode()
+        assert L.psr_batch_solve_noalloc(None, B, *([None] * 14), None, None) == -1
+        assert "work-queue limit" in L.psr_last_error().decode()
+        assert L.psr_batch_solve_soot(None, B, *([None] * 17), None, None) == -1
+        assert "work-queue limit" in L.psr_last_error().decode()
+        mechs = (ctypes.c_void_p * 1)(None)
+        assert L.psr_batch_solve_multi(mechs, 1, B, *([None] * 15), None, None) == -1
+        assert "work-queue limit" in L.psr_last_error().decode()
+    # at the limit the call goes on to the mechanism check
+    assert L.psr_batch_solve(None, (1 << 31) - (1 << 22), *([None] * 14), None, None) == -1
+    assert "mechanism is NULL" in L.psr_last_error().decode()

@@ -26,6 +26,18 @@ def env():
                 batch=synth.workload_batch(NAME, spec))
 
 
+_ROOTS = {}
+
+
+def _oracle_roots(idx):
+    """Oracle solves of sampled reactors of the sooting batch, cached across both forms."""
+    key = tuple(idx)
+    if key not in _ROOTS:
+        from tests import oracle_pool
+        _ROOTS[key] = oracle_pool.solve([(NAME, b) for b in idx])
+    return _ROOTS[key]
+
+
 def _t(env, b, keys=("Y_in", "T_in", "tau", "P", "Y0", "T0", "M_in")):
     import torch
     return {k: torch.tensor(getattr(b, k), dtype=torch.float64, device=env["dev"]) for k in keys}
@@ -85,7 +97,8 @@ def test_soot_jacobian_parity(env, precision):
 @pytest.mark.parametrize("precision", [psr.PSR_FP64, psr.PSR_MIXED])
 def test_soot_full_size_solve(env, precision):
     """The 16384-reactor launch: every converged reactor has ||F|| <= 1e-8 and conserves
-    carbon (gas + soot) to 1e-12; three sampled reactors match the oracle."""
+    carbon (gas + soot) to 1e-12; eight sampled reactors (oracle in a process pool) match
+    the oracle, at least six of them on the same branch."""
     batch, mech = env["batch"], env["mech"]
     t = _t(env, batch)
     out = psr.batch_solve_soot(env["gm"], t["Y_in"], t["T_in"], t["tau"], t["P"], t["M_in"], t["Y0"], t["T0"],
@@ -100,18 +113,25 @@ def test_soot_full_size_solve(env, precision):
     soot = (M[conv, 1] - batch.M_in[conv, 1]) / (rho * S.N_A)
     scale = ((Y[conv] + batch.Y_in[conv]) / mech.W) @ mech.comp[:, 0]
     assert np.max(np.abs(gas + soot) / scale) <= 1e-12
-    for b in (3, 6, 11):
-        inlet = O.inlet_of(batch, b)
-        r, Mo = S.solve_soot_reactor(mech, inlet, batch.Y0[b], batch.T0[b], batch.M_in[b])
-        if r.status != O.CONVERGED:
+    idx = (3, 6, 11, 257, 1900, 4711, 9001, 16000)
+    res = _oracle_roots(idx)
+    compared = 0
+    for b in idx:
+        x, status, Mo, _ = res[(NAME, b)]
+        if status != O.CONVERGED:
             continue
-        assert st[b] in psr.CONVERGED_STATES
-        if abs(T[b] - r.x[mech.K]) > 1.0:
-            continue                                   # another branch (checked as a root by the bound above)
-        big = r.x[:mech.K] > Y_MIN
-        assert np.max(np.abs(Y[b][big] - r.x[:mech.K][big]) / r.x[:mech.K][big]) <= Y_REL
-        assert abs(T[b] - r.x[mech.K]) <= T_ABS
+        assert st[b] in psr.CONVERGED_STATES, f"reactor {b}: GPU status {st[b]}, the oracle converged"
+        if abs(T[b] - x[mech.K]) > 1.0:
+            # another branch: it must be a root of the oracle's residual
+            from tests import oracle_pool
+            assert oracle_pool.root_residual(NAME, b, Y[b], T[b], M[b]) <= 1e-7, f"reactor {b}: not a root"
+            continue
+        big = x[:mech.K] > Y_MIN
+        assert np.max(np.abs(Y[b][big] - x[:mech.K][big]) / x[:mech.K][big]) <= Y_REL
+        assert abs(T[b] - x[mech.K]) <= T_ABS
         assert np.max(np.abs(M[b] - Mo) / Mo) <= M_REL
+        compared += 1
+    assert compared >= 6, f"only {compared} of {len(idx)} sampled sooting reactors compared within the bar"
 
 
 def test_mixed_fallback_resolves_in_fp64(env):

@@ -51,6 +51,25 @@ def test_monodisperse_coagulation_and_growth_closed_forms():
         np.testing.assert_allclose(W[0, r], exact, rtol=1e-10)
 
 
+@pytest.mark.parametrize("m", [32.0, 500.0, 2.0e4])
+def test_monodisperse_coagulation_higher_moments(m):
+    """Equal particles of m carbons: each free-molecular collision takes two m-particles
+    and makes one 2m-particle, at ½ β N² collisions per unit volume and time with
+    β = K_f (2/m)^(1/2) (2 m^(1/3))^2. So dM_r/dt = ½ β N² ((2m)^r − 2 m^r)
+    = ½ β N² m^r (2^r − 2) for every r: −½ β N² at r = 0, 0 at r = 1, and the
+    binomial sums of G_2..G_5 must add up to 2^r − 2."""
+    spec, mech, _ = _soot_mech()
+    sp = S.Soot(mech.soot)
+    N, T = 4e9, 1900.0
+    M = N * m ** np.arange(6.0)
+    _, _, G, _ = S.soot_sources(sp, M[None], np.array([1e-7]), np.array([T]))
+    Kf = sp.eps * (3 * S.M_C / (4 * math.pi * sp.rho_s)) ** (1 / 6) * (6 * S.K_B * T / sp.rho_s) ** 0.5
+    beta = Kf * math.sqrt(2.0 / m) * (2 * m ** (1 / 3)) ** 2
+    for r in range(6):
+        np.testing.assert_allclose(G[0, r], 0.5 * beta * N * N * m ** r * (2.0 ** r - 2.0), rtol=1e-10,
+                                   atol=1e-12 * beta * N * N * m ** r)
+
+
 def test_coagulation_conserves_carbon_and_reduces_number():
     spec, mech, _ = _soot_mech()
     sp = S.Soot(mech.soot)

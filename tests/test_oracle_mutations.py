@@ -69,6 +69,31 @@ def troe_without_broadening(mech, T, Pr):
     return np.ones_like(np.asarray(Pr))
 
 
+def _troe_with_t2_term(mech, T, Pr, t2_term):
+    """The Troe form of the oracle's docstring with the T** term of F_cent replaced by
+    t2_term(T, T2) (the planted mistakes below differ only there)."""
+    T = np.asarray(T)[:, None]
+    alpha, T3, T1, T2 = (mech.troe[None, :, j] for j in range(4))
+    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+        Fcent = (1 - alpha) * np.exp(-T / T3) + alpha * np.exp(-T / T1) + t2_term(T, T2)
+        lf = np.log10(Fcent)
+        c = -0.4 - 0.67 * lf
+        n = 0.75 - 1.27 * lf
+        u = np.log10(Pr) + c
+        f1 = u / (n - 0.14 * u)
+        return 10.0 ** (lf / (1 + f1 * f1))
+
+
+def troe_t2_inverted(mech, T, Pr):
+    """The T** term of F_cent written exp(-T/T**) instead of exp(-T**/T)."""
+    return _troe_with_t2_term(mech, T, Pr, lambda T_, T2: np.where(T2 != 0, np.exp(-T_ / T2), 0.0))
+
+
+def troe_t2_dropped(mech, T, Pr):
+    """F_cent without its T** term (the three-parameter form for every row)."""
+    return _troe_with_t2_term(mech, T, Pr, lambda T_, T2: 0.0 * T2)
+
+
 def wdot_sign(mech, q):
     """wdot = sum nu' q (reactant minus product): the sign of nu in Eq. (4) flipped."""
     return -_orig["net_production_rates"](mech, q)
@@ -160,6 +185,20 @@ def coagulation_grid_linear(logmu, x, y):
     return sum(w[l] * _orig_soot["grid_f"](logmu, l, x, y) for l in range(4))
 
 
+def coagulation_without_binomial(soot, M, CP, T):
+    """G_r = ½ K_f M_0² sum_k f(1/2)_{k,r-k}: the binomial weights C(r, k) of the
+    coagulation sums dropped (G_0 and G_1 unchanged)."""
+    R, W, G, s = _orig_soot["soot_sources"](soot, M, CP, T)
+    M = np.asarray(M)
+    logmu = np.log10(M / M[..., :1])
+    Kf = soot.eps * (3 * S.M_C / (4 * math.pi * soot.rho_s)) ** (1 / 6) * (6 * S.K_B * np.asarray(T) / soot.rho_s) ** 0.5
+    beta = Kf * M[..., 0] ** 2
+    G = np.array(G, copy=True)
+    for rr in range(2, S.NMOM):
+        G[..., rr] = 0.5 * beta * sum(S.f_half(logmu, k, rr - k) for k in range(1, rr))
+    return R, W, G, s
+
+
 def sensitivity_sign(mech, inlet, x, energy="adiabatic", lnmult=None):
     """S = +J^-1 dF/dp: the minus sign of the implicit-function theorem dropped."""
     return -_orig["sensitivities"](mech, inlet, x, energy, lnmult)
@@ -187,6 +226,10 @@ CASES = [
      [_call("test_third_body_isomerisation_closed_form"), _call("test_falloff_isomerisation_at_the_troe_centre")]),
     ("troe_broadening", troe_without_broadening,
      [_call("test_falloff_isomerisation_at_the_troe_centre"), _call("test_troe_centre_and_limits")]),
+    ("troe_broadening", troe_t2_inverted,
+     [_call("test_falloff_isomerisation_t2_term"), _call("test_troe_t2_term_alone", 1500.0)]),
+    ("troe_broadening", troe_t2_dropped,
+     [_call("test_falloff_isomerisation_t2_term"), _call("test_troe_t2_term_alone", 800.0)]),
     ("net_production_rates", wdot_sign, [_call("test_isomerisation_closed_form"),
                                          _call("test_dimerisation_closed_form")]),
     ("net_production_rates", wdot_reactants_only, [_call("test_wdot_conserves_mass_and_elements", "k10_b64")]),
@@ -208,6 +251,8 @@ SOOT_CASES = [
     ("soot_sources", nucleation_without_size, [_momic("test_nucleation_only_steady_state")]),
     ("soot_sources", growth_per_particle, [_momic("test_monodisperse_coagulation_and_growth_closed_forms")]),
     ("f_half", coagulation_grid_linear, [_momic("test_monodisperse_coagulation_and_growth_closed_forms")]),
+    ("soot_sources", coagulation_without_binomial,
+     [_call("test_monodisperse_coagulation_higher_moments", 500.0, module=momic_pins)]),
 ]
 
 

@@ -176,12 +176,10 @@ def test_third_body_isomerisation_closed_form():
     np.testing.assert_allclose(r.x[2], S - YA[0], rtol=1e-12)
 
 
-def test_falloff_isomerisation_at_the_troe_centre():
-    """A (+M) <=> B (+M), Troe falloff at the centre of the broadening curve (F = F_cent
-    = 1/2, golden file): k_f = k_inf P_r / (1 + P_r) / 2 with P_r = k_0 [M] / k_inf, then
-    the linear isomerisation closed form. Catches a missing Lindemann blend, a missing F,
-    [M] without efficiencies, and an extra [M] factor on a falloff rate of progress."""
-    mech = golden("troe_isomer.psrmech")
+def _falloff_isomer_closed_form(fixture):
+    """Fixed-T steady state of the falloff isomerisation fixtures (F = F_cent = 1/2 at the
+    centre of the broadening curve): the oracle's root and the closed-form Y_A, Y_B."""
+    mech = golden(fixture)
     T, tau, P = 1500.0, 1e-3, synth.ONE_ATM
     Y_in = np.array([0.5, 0.4, 0.1])
     inlet = O.Inlet(Y_in, 500.0, tau, P, T_spec=T)
@@ -196,6 +194,24 @@ def test_falloff_isomerisation_at_the_troe_centre():
     kf = k_inf * Pr / (1.0 + Pr) * 0.5
     kr = kf / math.exp((5.5 - 6.0) - (1500.0 - 2000.0) / T)
     YA = (Y_in[1] + tau * kr * S) / (1.0 + tau * (kf + kr))
+    return r, YA, S
+
+
+def test_falloff_isomerisation_at_the_troe_centre():
+    """A (+M) <=> B (+M), Troe falloff at the centre of the broadening curve (F = F_cent
+    = 1/2, golden file): k_f = k_inf P_r / (1 + P_r) / 2 with P_r = k_0 [M] / k_inf, then
+    the linear isomerisation closed form. Catches a missing Lindemann blend, a missing F,
+    [M] without efficiencies, and an extra [M] factor on a falloff rate of progress."""
+    r, YA, S = _falloff_isomer_closed_form("troe_isomer.psrmech")
+    np.testing.assert_allclose(r.x[1], YA, rtol=1e-12)
+    np.testing.assert_allclose(r.x[2], S - YA, rtol=1e-12)
+
+
+def test_falloff_isomerisation_t2_term():
+    """The same closed form with F_cent = 1/2 made by the four-parameter T** term alone
+    (alpha = 0, T*** -> 0+, T** = T ln 2; golden file). Catches the T** term read as
+    exp(-T/T**) (F_cent = 0.236) or dropped (F_cent = 0)."""
+    r, YA, S = _falloff_isomer_closed_form("troe_t2_isomer.psrmech")
     np.testing.assert_allclose(r.x[1], YA, rtol=1e-12)
     np.testing.assert_allclose(r.x[2], S - YA, rtol=1e-12)
 
@@ -210,6 +226,22 @@ def test_troe_fcent_one_is_lindemann():
     Pr = np.logspace(-8, 8, 17)[None, :].T
     F = O.troe_broadening(m, np.full(17, 1500.0), Pr)
     np.testing.assert_allclose(F, 1.0, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("T", [800.0, 1500.0, 2600.0])
+def test_troe_t2_term_alone(T):
+    """alpha = 0 and T*** -> 0+ leave F_cent = exp(-T**/T); with T** = T ln 2 that is 1/2,
+    and at the centre log10 P_r = -c the broadening factor equals F_cent. A second T**
+    (= T ln 4, F_cent = 1/4) checks the exponent's scaling, and the centre of each lies
+    where F is smallest."""
+    for t2, fc in ((T * math.log(2.0), 0.5), (T * math.log(4.0), 0.25)):
+        m = _troe(0.0, 1e-30, 1.0, t2)
+        c = -0.4 - 0.67 * math.log10(fc)
+        F = O.troe_broadening(m, np.array([T]), np.array([[10.0 ** (-c)]]))[0, 0]
+        np.testing.assert_allclose(F, fc, rtol=1e-13)
+        pr = 10.0 ** (-c + np.linspace(-3, 3, 61))
+        Fs = O.troe_broadening(m, np.full(1, T), pr[None, :])[0]
+        assert np.all(Fs >= fc * (1 - 1e-13)) and np.argmin(Fs) == 30
 
 
 def test_troe_centre_and_limits():
