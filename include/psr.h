@@ -47,11 +47,13 @@ extern "C" {
 #define PSR_MAX_ITER 1      /* max_newton Newton iterations used */
 #define PSR_NONFINITE 2     /* the residual at the initial guess is not finite */
 #define PSR_TS_EXHAUSTED 4  /* max_ts_rounds time-stepping rounds, or dt collapsed */
-#define PSR_BAD_INPUT 7
-#define PSR_JAC_ANALYTIC 0
-#define PSR_JAC_FD 1      /* psr_batch_solve_multi: mechanism id out of range, not solved */
 #define PSR_REFINE_FALLBACK 5 /* PSR_MIXED: converged (same criterion) after the FP32-Jacobian
                                  launch left it unconverged and the FP64 re-solve succeeded */
+#define PSR_BAD_INPUT 7     /* psr_batch_solve_multi: mechanism id out of range, not solved */
+
+/* Jacobian of the Newton iteration (options.jacobian) */
+#define PSR_JAC_ANALYTIC 0
+#define PSR_JAC_FD 1        /* central differences, as the paper builds it (Sec. 1) */
 
 /* precision of the Jacobian and its LU factors (the residual is always FP64) */
 #define PSR_FP64 0
@@ -118,8 +120,16 @@ typedef struct {
                                (pseudo-transient continuation; dt grown by 2 x the ||F|| ratio
                                clipped to [0.1, 8]); later steps, and all steps when 0, are
                                solved by damped Newton (<= ts_newton iterations, to ts_rtol) */
-    int32_t reserved[2];
+    int32_t path;           /* PSR_PATH_AUTO (default): one warp per reactor when K + 1 <= 64,
+                               else one 512-thread block; PSR_PATH_WARP / PSR_PATH_BLOCK force
+                               one (PSR_E_UNSUPPORTED where the mechanism does not fit it) */
+    int32_t reserved[1];
 } psr_options;
+
+/* threads per reactor (psr_options.path) */
+#define PSR_PATH_AUTO 0
+#define PSR_PATH_WARP 1     /* one warp per reactor, K + 1 <= 64 (gas, or gas + soot with K + 7 <= 64) */
+#define PSR_PATH_BLOCK 2    /* one 512-thread block per reactor, gas mechanisms with K + 1 <= 512 */
 
 void psr_options_default(psr_options *o);
 
@@ -238,12 +248,14 @@ int psr_eval_jacobian_fd(const psr_mech *m, int64_t B,
 /* Autotuner for the launch shape (the paper has no counterpart; a service of the
  * library): solves the caller's sample batch (device arrays as psr_batch_solve, B >= 1,
  * ideally a few thousand reactors like the production batches) once per candidate shape
- * and writes the one with the most converged solves per second into opt->warps_per_block
- * and opt->blocks_per_sm; every other field of *opt is used as given. Candidates on the
- * warp path: 1..4 warps per block, and 2-warp blocks capped at 2..4 blocks per SM; the
- * block path (K + 1 > 64) has a single shape (warps_per_block = 0, blocks_per_sm = 0).
- * Synchronises cuda_stream; allocates and frees output scratch on it. Results of the
- * solver do not depend on the shape (one warp per reactor either way).
+ * and writes the one with the most converged solves per second into opt->path,
+ * opt->warps_per_block and opt->blocks_per_sm; every other field of *opt is used as
+ * given. Candidates for K + 1 <= 64: one warp per reactor with 1..4 warps per block and
+ * 2-warp blocks capped at 2..4 blocks per SM, and one 512-thread block per reactor;
+ * larger mechanisms have the block path only. Synchronises cuda_stream; allocates and
+ * frees output scratch on it. The roots do not depend on the shape: within a path the
+ * arithmetic is the same, and the two paths reach the same roots within the solver's
+ * tolerance (the block path's Jacobian sums its contributions in another order).
  * Errors: PSR_E_ARG (NULL, soot mechanism, B outside 1..2^24), PSR_E_CUDA, PSR_E_OOM. */
 int psr_autotune(const psr_mech *m, int64_t B,
                  const double *Y_in, const double *T_in, const double *tau, const double *P,

@@ -10,7 +10,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpsr.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["psr_solve.cu", "psr_block.cu", "mech.cpp"]
+SOURCES = ["psr_solve.cu", "psr_block.cu", "mech.cpp", "pipe_probe.cu"]
 # psr_solve_inst.cu is built once per solve_kernel instantiation (Jacobian precision,
 # soot, finite-difference Jacobian): six objects that compile in parallel.
 INSTANCES = [(tj, soot, fdj) for soot, fdj in ((0, 0), (0, 1), (1, 0)) for tj in ("float", "double")]
@@ -39,7 +39,7 @@ def _compile(unit, nvcc):
 def build(force=False):
     """Compile every translation unit and link libpsr.so; returns the library path."""
     srcs = ([os.path.join(CSRC, s) for s in SOURCES + ["psr_solve_inst.cu"] + HEADERS]
-            + [os.path.join(INCLUDE, "psr.h")])
+            + [os.path.join(INCLUDE, h) for h in ("psr.h", "psr_probe.h")])
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(s) <= t for s in srcs) and os.path.getmtime(__file__) <= t:

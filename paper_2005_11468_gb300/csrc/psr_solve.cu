@@ -318,7 +318,7 @@ int check_opts(const psr_options *po) {
         (s.energy != PSR_ADIABATIC && s.energy != PSR_FIXED_T) || s.warps_per_block < 0 || s.warps_per_block > 32 ||
         s.blocks_per_sm < 0 || (s.mixed_fallback != 0 && s.mixed_fallback != 1) ||
         (s.jacobian != PSR_JAC_ANALYTIC && s.jacobian != PSR_JAC_FD) || s.mixed_max_newton < 0 || s.jac_age < 0 ||
-        s.jac_age > 64 || s.ts_linear < 0)
+        s.jac_age > 64 || s.ts_linear < 0 || s.path < PSR_PATH_AUTO || s.path > PSR_PATH_BLOCK)
         return set_error(PSR_E_ARG, "psr_options: value out of range");
     return PSR_OK;
 }
@@ -583,10 +583,15 @@ int psr_batch_solve(const psr_mech *m, int64_t B, const double *Y_in, const doub
     psr_options_default(&d);
     const psr_options &po = opt ? *opt : d;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    if (po.jacobian == PSR_JAC_FD && !warp_path(m))
-        return set_error(PSR_E_UNSUPPORTED, "finite-difference Jacobian: K + 1 <= 64 only");
-    if (!warp_path(m))
+    const bool block = po.path == PSR_PATH_BLOCK || !warp_path(m);
+    if (po.path == PSR_PATH_WARP && !warp_path(m))
+        return set_error(PSR_E_UNSUPPORTED, "PSR_PATH_WARP: K + 1 <= 64 only");
+    if (po.jacobian == PSR_JAC_FD && block)
+        return set_error(PSR_E_UNSUPPORTED, "finite-difference Jacobian: the warp path (K + 1 <= 64) only");
+    if (block) {
+        if ((rc = block_check(m->m))) return rc;
         return block_solve(m->m, bt, o, po.precision, po.mixed_fallback != 0, po.blocks_per_sm, st);
+    }
     if (po.precision == PSR_MIXED)
         return launch_mixed(m->m, bt, o, po.warps_per_block, po.blocks_per_sm, po.mixed_fallback != 0, st);
     return launch_solve<double>(m->m, bt, o, po.warps_per_block, po.blocks_per_sm, st);
@@ -604,8 +609,8 @@ int psr_batch_solve_noalloc(const psr_mech *m, int64_t B, const double *Y_in, co
     if (rc) return rc;
     if (m->m.has_soot)
         return set_error(PSR_E_ARG, "mechanism carries soot: use the _soot entry points");
-    if (!warp_path(m))
-        return set_error(PSR_E_UNSUPPORTED, "psr_batch_solve_noalloc: at most 64 unknowns (K + 1)");
+    if (!warp_path(m) || (opt && opt->path == PSR_PATH_BLOCK))
+        return set_error(PSR_E_UNSUPPORTED, "psr_batch_solve_noalloc: the warp path (K + 1 <= 64) only");
     if (B == 0) return PSR_OK;
     if (!Y_in || !T_in || !tau || !P || !Y0 || !T0 || !Y_out || !T_out)
         return set_error(PSR_E_ARG, "psr_batch_solve_noalloc: required pointer is NULL");
@@ -631,6 +636,7 @@ int psr_batch_solve_soot(const psr_mech *m, int64_t B, const double *Y_in, const
     int rc = check_mech(m);
     if (rc) return rc;
     if (!m->m.has_soot) return set_error(PSR_E_ARG, "mechanism has no soot record: use psr_batch_solve");
+    if (opt && opt->path == PSR_PATH_BLOCK) return set_error(PSR_E_UNSUPPORTED, "soot: the warp path only");
     if (B == 0) return PSR_OK;
     if (!Y_in || !T_in || !tau || !P || !M_in || !Y0 || !T0 || !Y_out || !T_out || !M_out)
         return set_error(PSR_E_ARG, "psr_batch_solve_soot: required pointer is NULL");
@@ -878,7 +884,9 @@ int psr_batch_solve_multi(const psr_mech *const *mechs, int32_t n_mech, int64_t 
         bt.list_len = counts + c;
         bt.row_off = row_off;
         const Mech &mm = mechs[c]->m;
-        if (!warp_path(mechs[c]))
+        if (po.path == PSR_PATH_WARP && !warp_path(mechs[c]))
+            rc = set_error(PSR_E_UNSUPPORTED, "PSR_PATH_WARP: K + 1 <= 64 only");
+        else if (po.path == PSR_PATH_BLOCK || !warp_path(mechs[c]))
             rc = block_solve(mm, bt, o, po.precision, po.mixed_fallback != 0, po.blocks_per_sm, sc);
         else if (po.precision == PSR_MIXED)
             rc = launch_mixed(mm, bt, o, po.warps_per_block, po.blocks_per_sm, po.mixed_fallback != 0, sc);
@@ -908,15 +916,18 @@ int psr_autotune(const psr_mech *m, int64_t B, const double *Y_in, const double 
     double *Yo = reinterpret_cast<double *>(buf), *To = Yo + nb * K, *fn = To + nb;
     int32_t *it = reinterpret_cast<int32_t *>(fn + nb), *ts = it + nb, *stt = ts + nb, *nf = stt + nb;
     // candidates: warps per block x block cap on the warp path; the block path has one shape
+    // candidates: threads per reactor (a warp, or a 512-thread block for gas mechanisms),
+    // and on the warp path warps per block x block cap
     struct Cand {
-        int wpb, bps;
+        int wpb, bps, path;
     };
     std::vector<Cand> cands;
     if (warp_path(m)) {
-        for (int w : {1, 2, 3, 4}) cands.push_back({w, 0});
-        for (int b : {2, 3, 4}) cands.push_back({2, b});
+        for (int w : {1, 2, 3, 4}) cands.push_back({w, 0, PSR_PATH_WARP});
+        for (int b : {2, 3, 4}) cands.push_back({2, b, PSR_PATH_WARP});
+        if (!m->m.has_soot) cands.push_back({0, 0, PSR_PATH_BLOCK});
     } else {
-        cands.push_back({0, 0});
+        cands.push_back({0, 0, PSR_PATH_BLOCK});
     }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -929,6 +940,7 @@ int psr_autotune(const psr_mech *m, int64_t B, const double *Y_in, const double 
     for (size_t c = 0; c < cands.size() && rc == PSR_OK; ++c) {
         trial.warps_per_block = cands[c].wpb;
         trial.blocks_per_sm = cands[c].bps;
+        trial.path = cands[c].path;
         cudaEventRecord(e0, st);
         rc = psr_batch_solve(m, B, Y_in, T_in, tau, P, Y0, T0, nullptr, Yo, To, it, ts, stt, fn, nf, &trial, st);
         cudaEventRecord(e1, st);
@@ -959,6 +971,7 @@ int psr_autotune(const psr_mech *m, int64_t B, const double *Y_in, const double 
     if (rc == PSR_OK) {
         opt->warps_per_block = best.wpb;
         opt->blocks_per_sm = best.bps;
+        opt->path = best.path;
     }
     return rc;
 }

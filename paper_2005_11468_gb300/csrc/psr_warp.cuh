@@ -44,6 +44,18 @@ namespace {
 #ifndef PSR_STAGE
 #define PSR_STAGE
 #endif
+#ifndef PSR_STAGE_F
+#define PSR_STAGE_F PSR_STAGE
+#endif
+#ifndef PSR_STAGE_J
+#define PSR_STAGE_J PSR_STAGE
+#endif
+#ifndef PSR_STAGE_LU
+#define PSR_STAGE_LU PSR_STAGE
+#endif
+#ifndef PSR_STAGE_SOLVE
+#define PSR_STAGE_SOLVE PSR_STAGE
+#endif
 // A length-n vector distributed over the warp: lane l holds components l and l + 32.
 struct V2 {
     double a, b;
@@ -192,7 +204,7 @@ __device__ __forceinline__ void soot_eval(const double *__restrict__ st, const d
 // evaluation: thermo, k_f and k_r of elementary and third-body reactions are reused from
 // the caches (rate constants depend on T only); falloff rows are recomputed ([M] moves).
 template <class TJ, bool SOOT, bool FRZ = false>
-__device__ PSR_STAGE void eval_F(const DevMech &M, const WS<TJ> &w, const V2 &y, V2 &F, Mix &mx, SpecLane &sl,
+__device__ PSR_STAGE_F void eval_F(const DevMech &M, const WS<TJ> &w, const V2 &y, V2 &F, Mix &mx, SpecLane &sl,
                        const double *Yin_row, const double *Min, double tau, double P, double Tspec, int energy,
                        const double *__restrict__ mult) {
     const int lane = threadIdx.x & 31;
@@ -417,7 +429,7 @@ __device__ PSR_STAGE void eval_F(const DevMech &M, const WS<TJ> &w, const V2 &y,
 // s_k = sum_l Jc_kl [X_l] and T-derivatives wT_k, then the transform to (Y, T) through
 // rho(Y, T) and the energy row of Eq. (3). Entries are accumulated in TJ.
 template <class TJ, bool SOOT>
-__device__ PSR_STAGE void eval_J(const DevMech &M, const WS<TJ> &w, const V2 &y, const V2 &c, const Mix &mx,
+__device__ PSR_STAGE_J void eval_J(const DevMech &M, const WS<TJ> &w, const V2 &y, const V2 &c, const Mix &mx,
                                  const SpecLane &sl, const double *Yin_row, const double *Min, double tau,
                                  int energy, const double *__restrict__ mult) {
     const int lane = threadIdx.x & 31;
@@ -737,7 +749,7 @@ __device__ void eval_J_fd(const DevMech &M, const WS<TJ> &w, const V2 &y, const 
 // In-place LU of w.J (n x n) with row interchanges; perm holds the final row order.
 // Returns false on a zero or non-finite pivot.
 template <class TJ>
-__device__ PSR_STAGE bool lu_factor(const WS<TJ> &w, int n) {
+__device__ PSR_STAGE_LU bool lu_factor(const WS<TJ> &w, int n) {
     const int lane = threadIdx.x & 31;
     const int P = w.P;
     for (int j = lane; j < n; j += 32) w.perm[j] = int16_t(j);
@@ -797,7 +809,7 @@ __device__ PSR_STAGE bool lu_factor(const WS<TJ> &w, int n) {
 
 // Solve (LU) x = -r with r distributed (V2), x returned as V2 (FP64 promote).
 template <class TJ>
-__device__ PSR_STAGE void lu_solve_neg(const WS<TJ> &w, int n, const V2 &r, V2 &x) {
+__device__ PSR_STAGE_SOLVE void lu_solve_neg(const WS<TJ> &w, int n, const V2 &r, V2 &x) {
     const int lane = threadIdx.x & 31;
     const int P = w.P;
     // rhs[k] = -r[perm[k]]: stage r in rhs via the permutation

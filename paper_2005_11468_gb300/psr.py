@@ -22,6 +22,7 @@ PSR_JAC_ANALYTIC, PSR_JAC_FD = 0, 1
 CONVERGED_STATES = (PSR_CONVERGED, PSR_REFINE_FALLBACK)
 PSR_FP64, PSR_MIXED = 0, 1
 PSR_ADIABATIC, PSR_FIXED_T = 0, 1
+PSR_PATH_AUTO, PSR_PATH_WARP, PSR_PATH_BLOCK = 0, 1, 2
 
 
 class PsrError(RuntimeError):
@@ -48,7 +49,8 @@ class COptions(ctypes.Structure):
                 ("energy", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("mixed_fallback", ctypes.c_int32),
                 ("jacobian", ctypes.c_int32), ("mixed_max_newton", ctypes.c_int32),
-                ("jac_age", ctypes.c_int32), ("ts_linear", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("jac_age", ctypes.c_int32), ("ts_linear", ctypes.c_int32), ("path", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 _lib = None
@@ -87,6 +89,7 @@ def lib():
         L.psr_autotune.argtypes = [vp, i64] + [dp] * 6 + [ctypes.POINTER(COptions), vp]
         L.psr_batch_solve_multi.argtypes = [ctypes.POINTER(vp), i32, i64, dp, dp] + [dp] * 8 + [dp] * 5 + \
             [ctypes.POINTER(COptions), vp]
+        L.psr_pipe_probe.argtypes = [i32, i64, i32, i32, dp, vp]
         _lib = L
     return _lib
 
@@ -124,6 +127,7 @@ class Options:
     mixed_max_newton: int = 300
     jac_age: int = 1
     ts_linear: int = 150
+    path: int = 0
 
     def to_c(self):
         o = COptions()
@@ -423,7 +427,7 @@ def autotune(mech: Mechanism, Y_in, T_in, tau, P, Y0, T0, opts: Options = None) 
         mech.handle, B, _ptr(Y_in, f64, (B, K), "Y_in"), _ptr(T_in, f64, (B,), "T_in"), _ptr(tau, f64, (B,), "tau"),
         _ptr(P, f64, (B,), "P"), _ptr(Y0, f64, (B, K), "Y0"), _ptr(T0, f64, (B,), "T0"), ctypes.byref(o),
         _stream()))
-    return dataclasses.replace(base, warps_per_block=o.warps_per_block, blocks_per_sm=o.blocks_per_sm)
+    return dataclasses.replace(base, warps_per_block=o.warps_per_block, blocks_per_sm=o.blocks_per_sm, path=o.path)
 
 
 def eval_rates(mech: Mechanism, Y, T, P, rate_mult=None, out=None):
@@ -442,3 +446,19 @@ def eval_rates(mech: Mechanism, Y, T, P, rate_mult=None, out=None):
         _ptr(out.get("kr"), f64, (B, mech.I)), _ptr(out.get("q"), f64, (B, mech.I)),
         _ptr(out.get("wdot"), f64, (B, K)), _stream()))
     return out
+
+
+PROBE_FMA64, PROBE_FMA32, PROBE_EXP64, PROBE_LOG64, PROBE_DIV64 = 0, 1, 2, 3, 4
+# operations per thread and iteration of each probe (psr_probe.h): flops for the FMA
+# probes, calls for exp / log / division
+PROBE_OPS = {PROBE_FMA64: 16, PROBE_FMA32: 32, PROBE_EXP64: 8, PROBE_LOG64: 8, PROBE_DIV64: 8}
+
+
+def pipe_probe(kind, iters, blocks, threads, sink):
+    """psr_pipe_probe: one probe launch on the current stream; `sink` is a float64 CUDA
+    tensor of at least blocks x threads elements. Returns the operation count."""
+    import torch
+    if sink.numel() < blocks * threads:
+        raise ValueError("sink too small")
+    _check(lib().psr_pipe_probe(kind, iters, blocks, threads, _ptr(sink, torch.float64, None, "sink"), _stream()))
+    return PROBE_OPS[kind] * blocks * threads * iters

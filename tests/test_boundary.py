@@ -22,14 +22,18 @@ def L():
 
 
 def declared_functions():
-    text = open(os.path.join(ROOT, "include", "psr.h")).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(psr_\w+)\s*\(", text)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(psr_\w+)\s*\(", text))
+    return sorted(names)
 
 
 def test_exports_every_declared_symbol(L):
     names = declared_functions()
-    assert "psr_batch_solve" in names and "psr_mech_load" in names
+    assert "psr_batch_solve" in names and "psr_mech_load" in names and "psr_pipe_probe" in names
     for n in names:
         assert hasattr(L, n), n
 
