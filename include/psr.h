@@ -123,8 +123,27 @@ typedef struct {
     int32_t path;           /* PSR_PATH_AUTO (default): one warp per reactor when K + 1 <= 64,
                                else one 512-thread block; PSR_PATH_WARP / PSR_PATH_BLOCK force
                                one (PSR_E_UNSUPPORTED where the mechanism does not fit it) */
-    int32_t reserved[1];
+    int32_t handoff;        /* -1 (default: 75 for PSR_FP64, 0 for PSR_MIXED) or 0..100. One warp
+                               per reactor only: once this percentage of the launch's working
+                               warps found its work queue empty, the reactors still running stop
+                               at their next Newton iteration and a second launch continues them
+                               from their iterates with one thread block each, in the same
+                               precision (PSR_MIXED: then the FP64 re-solve takes what is left).
+                               0 = off. Gas mechanisms, analytic Jacobian. Which reactors are
+                               handed over depends on timing, so results are reproducible to the
+                               solver's tolerance, not bit for bit; 0 gives bit-identical runs. */
+    int32_t lu_tensor;      /* PSR_LU_CUDA_CORES (default), PSR_LU_TF32 or PSR_LU_3XTF32: with
+                               PSR_MIXED on the block solver (K + 1 >= 96), the LU's trailing
+                               update A22 -= L21 U12 runs on the fifth-generation tensor cores
+                               (tcgen05, TF32 operands, FP32 accumulation in tensor memory);
+                               3XTF32 splits each operand into two TF32 parts (three products)
+                               for FP32-like accuracy. Other solves ignore it. */
 } psr_options;
+
+/* LU trailing update (psr_options.lu_tensor) */
+#define PSR_LU_CUDA_CORES 0
+#define PSR_LU_TF32 1
+#define PSR_LU_3XTF32 3
 
 /* threads per reactor (psr_options.path) */
 #define PSR_PATH_AUTO 0
@@ -322,6 +341,14 @@ int psr_batch_adjoint(const psr_mech *m, int64_t B,
  * (1 = factored, 0 = zero or non-finite pivot), n <= 64. PSR_MIXED factors in FP32. */
 int psr_batch_lu_solve(int64_t B, int32_t n, const double *A, const double *r,
                        double *x_out, int32_t *ok_out, int32_t precision, void *cuda_stream);
+
+/* psr_batch_lu_solve in FP32 with the LU's trailing update on the tensor cores (the
+ * Sec. 1 / Sec. 3 LU of the mixed form's large-mechanism path): lu_tensor is PSR_LU_TF32
+ * or PSR_LU_3XTF32 (PSR_LU_CUDA_CORES gives the FP32 CUDA-core LU). Sizes with n < 96 have
+ * no trailing matrix large enough and use CUDA cores throughout. Arguments, layout and
+ * errors as psr_batch_lu_solve. */
+int psr_batch_lu_solve_tc(int64_t B, int32_t n, const double *A, const double *r, double *x_out, int32_t *ok_out,
+                          int32_t lu_tensor, void *cuda_stream);
 
 const char *psr_last_error(void);
 

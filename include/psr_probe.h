@@ -13,6 +13,10 @@
  *                    accumulate per call)
  *   PSR_PROBE_LOG64  8 calls log(x) in FP64 per iteration (same overhead)
  *   PSR_PROBE_DIV64  8 FP64 divisions per iteration (same overhead)
+ *   PSR_PROBE_SATOM32 / _SAME  8 shared-memory float atomicAdd per iteration, each warp's
+ *                    lanes to 32 distinct words / all to one word (full collision)
+ *   PSR_PROBE_SATOM64 / _SAME  the same with double
+ * threads: a multiple of 32, at most 256.
  * The operation count of a launch is blocks x threads x iters x the per-iteration count;
  * the caller times the launch (CUDA events on `stream`). `sink` (device, >= blocks x
  * threads doubles) receives one value per thread so that no chain is optimised away.
@@ -31,6 +35,10 @@ extern "C" {
 #define PSR_PROBE_EXP64 2
 #define PSR_PROBE_LOG64 3
 #define PSR_PROBE_DIV64 4
+#define PSR_PROBE_SATOM32 5
+#define PSR_PROBE_SATOM32_SAME 6
+#define PSR_PROBE_SATOM64 7
+#define PSR_PROBE_SATOM64_SAME 8
 
 int psr_pipe_probe(int32_t kind, int64_t iters, int32_t blocks, int32_t threads, double *sink, void *stream);
 

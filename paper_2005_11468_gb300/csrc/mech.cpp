@@ -364,7 +364,8 @@ int upload(Mech &m) {
     std::vector<double> invW(m.K);
     for (int k = 0; k < m.K; ++k) invW[k] = 1.0 / m.W[k];
     std::vector<float> invW_f(invW.begin(), invW.end()), eff_val_f(m.eff_val.begin(), m.eff_val.end());
-    size_t oinvWf, oeffvf;
+    std::vector<float> beta_f(m.beta.begin(), m.beta.end()), theta_f(m.theta.begin(), m.theta.end());
+    size_t oinvWf, oeffvf, obetaf, othetaf;
     size_t oW, oinvW, onasa, olnA, obeta, otheta, oslots, odnu, otype, oeffp, oeffs, oeffv, otr, otroe,
         osp, ospr, ospn, opart, opartnu, opfm, oprm, oorig, odnud, ospnd, osoot;
     std::vector<double> dnu_d(m.dnu.begin(), m.dnu.end()), sp_nu_d(m.sp_nu.begin(), m.sp_nu.end());
@@ -372,6 +373,8 @@ int upload(Mech &m) {
     place(blob, invW, oinvW);
     place(blob, invW_f, oinvWf);
     place(blob, eff_val_f, oeffvf);
+    place(blob, beta_f, obetaf);
+    place(blob, theta_f, othetaf);
     place(blob, m.nasa, onasa);
     place(blob, m.lnA, olnA);
     place(blob, m.beta, obeta);
@@ -418,6 +421,8 @@ int upload(Mech &m) {
     D.invW = reinterpret_cast<const double *>(b + oinvW);
     D.invW_f = reinterpret_cast<const float *>(b + oinvWf);
     D.eff_val_f = reinterpret_cast<const float *>(b + oeffvf);
+    D.beta_f = reinterpret_cast<const float *>(b + obetaf);
+    D.theta_f = reinterpret_cast<const float *>(b + othetaf);
     D.nasa = reinterpret_cast<const double *>(b + onasa);
     D.lnA = reinterpret_cast<const double *>(b + olnA);
     D.beta = reinterpret_cast<const double *>(b + obeta);
@@ -540,6 +545,7 @@ void psr_options_default(psr_options *o) {
     o->mixed_max_newton = 300;
     o->jac_age = 1;
     o->ts_linear = 150;
+    o->handoff = -1;
 }
 
 }  // extern "C"

@@ -70,13 +70,32 @@ __global__ void math64_probe(int64_t iters, double *sink) {
     sink[t] = s;
 }
 
+// kinds 5-8: shared-memory atomicAdd of float / double, 8 per iteration, to 32 distinct
+// words per warp (lane-indexed) or all lanes to one word (the worst collision)
+template <class T, bool SAME>
+__global__ void smem_atomic_probe(int64_t iters, double *sink) {
+    __shared__ T buf[8 * 32 * 8];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, wid = (threadIdx.x >> 5) & 7;
+    for (int i = threadIdx.x; i < 8 * 32 * 8; i += blockDim.x) buf[i] = T(0);
+    __syncthreads();
+    T *base = buf + wid * 32 * 8;
+    const T v = T(1) + T(lane) * T(1e-3);
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) atomicAdd(base + c * 32 + (SAME ? 0 : lane), v);
+    }
+    __syncthreads();
+    sink[t] = double(buf[threadIdx.x % (8 * 32 * 8)]);
+}
+
 }  // namespace
 }  // namespace psr
 
 extern "C" int psr_pipe_probe(int32_t kind, int64_t iters, int32_t blocks, int32_t threads, double *sink,
                               void *stream) {
     using namespace psr;
-    if (iters < 1 || blocks < 1 || threads < 32 || threads > 1024 || !sink)
+    if (iters < 1 || blocks < 1 || threads < 32 || threads > 256 || (threads & 31) || !sink)
         return set_error(PSR_E_ARG, "psr_pipe_probe: bad sizes or NULL sink");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     switch (kind) {
@@ -85,6 +104,10 @@ extern "C" int psr_pipe_probe(int32_t kind, int64_t iters, int32_t blocks, int32
         case PSR_PROBE_EXP64: math64_probe<2><<<blocks, threads, 0, st>>>(iters, sink); break;
         case PSR_PROBE_LOG64: math64_probe<3><<<blocks, threads, 0, st>>>(iters, sink); break;
         case PSR_PROBE_DIV64: math64_probe<4><<<blocks, threads, 0, st>>>(iters, sink); break;
+        case PSR_PROBE_SATOM32: smem_atomic_probe<float, false><<<blocks, threads, 0, st>>>(iters, sink); break;
+        case PSR_PROBE_SATOM32_SAME: smem_atomic_probe<float, true><<<blocks, threads, 0, st>>>(iters, sink); break;
+        case PSR_PROBE_SATOM64: smem_atomic_probe<double, false><<<blocks, threads, 0, st>>>(iters, sink); break;
+        case PSR_PROBE_SATOM64_SAME: smem_atomic_probe<double, true><<<blocks, threads, 0, st>>>(iters, sink); break;
         default: return set_error(PSR_E_ARG, "psr_pipe_probe: unknown kind");
     }
     const cudaError_t e = cudaGetLastError();

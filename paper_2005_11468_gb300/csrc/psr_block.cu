@@ -14,6 +14,7 @@
 
 #include "psr_device.cuh"
 #include "psr_internal.h"
+#include "psr_tc.cuh"
 
 namespace psr {
 namespace {
@@ -33,12 +34,27 @@ struct BWS {
     double *v, *ra, *rb;      // [K] wdot / dense third-body column part; row coefficients
     double *tD, *tX;          // [n_troe] falloff derivative caches
     double *red;              // [kRedSlots][kBW] reduction partials
-    int *ired;                // [2][kBW] pivot-search partials (double-buffered), then the work-queue slot
+    int *ired;                // [2][kBW] pivot-search partials (double-buffered), the work-queue
+                              // slot, the tensor-core phase and failure flag
     TJ *J;                    // [n][P]
     TJ *rhs;                  // [n]
     int16_t *perm;            // [n]
     int P;
+    // tensor-core trailing update (FP32 Jacobian only): mode 0 = off, 1 = TF32, 3 = 3xTF32
+    int tc;
+    uint64_t *bar;            // mbarrier of the MMA completions
+    uint32_t *tmem_slot;      // tensor-memory base address of the accumulator
+    char *stage;              // kStageBytes of operand tiles (128-byte aligned)
 };
+
+// Operand staging of the tensor-core update: hi and lo TF32 parts of a 128 x 16 L21 tile
+// and of a 128 x 16 U12 tile (8 KB each). It reuses the rate arrays (kf, kr, q), which are
+// dead between the Jacobian assembly and the next residual, when they are large enough.
+constexpr int kStageBytes = 4 * 8192;
+constexpr int kTcMinM = 64;      // smallest trailing matrix updated on the tensor cores
+constexpr int kIred = 2 * kBW + 8;
+
+__host__ __device__ inline bool stage_in_rates(int I) { return size_t(3) * I * 8 >= size_t(kStageBytes) + 128; }
 
 __host__ __device__ inline int pitch_of(int n) { return (n & 1) ? n : n + 1; }
 
@@ -52,17 +68,18 @@ __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(
 // Shared-memory bytes of one block: the vector/table part, rhs and perm, and the
 // Jacobian itself when j_in_smem.
 template <class TJ>
-__host__ __device__ inline size_t bws_bytes(int K, int I, int nt, int n, bool j_in_smem) {
+__host__ __device__ inline size_t bws_bytes(int K, int I, int nt, int n, bool j_in_smem, bool tc = false) {
     size_t b = align16(sizeof(double) * bws_doubles(K, I, nt, n));
-    b = align16(b + sizeof(int) * (2 * kBW + 4));
+    b = align16(b + sizeof(int) * kIred);
     b = align16(b + sizeof(TJ) * n);
     b = align16(b + sizeof(int16_t) * n);
     if (j_in_smem) b = align16(b + sizeof(TJ) * size_t(n) * pitch_of(n));
+    if (tc && !stage_in_rates(I)) b = align16(b + kStageBytes + 128);
     return b;
 }
 
 template <class TJ>
-__device__ BWS<TJ> bcarve(char *base, int K, int I, int nt, int n, TJ *Jglobal) {
+__device__ BWS<TJ> bcarve(char *base, int K, int I, int nt, int n, TJ *Jglobal, int tc = 0) {
     BWS<TJ> w;
     double *d = reinterpret_cast<double *>(base);
     w.x = d;
@@ -96,14 +113,135 @@ __device__ BWS<TJ> bcarve(char *base, int K, int I, int nt, int n, TJ *Jglobal) 
     w.red = d;
     size_t off = align16(sizeof(double) * bws_doubles(K, I, nt, n));
     w.ired = reinterpret_cast<int *>(base + off);
-    off = align16(off + sizeof(int) * (2 * kBW + 4));
+    off = align16(off + sizeof(int) * kIred);
     w.rhs = reinterpret_cast<TJ *>(base + off);
     off = align16(off + sizeof(TJ) * n);
     w.perm = reinterpret_cast<int16_t *>(base + off);
     off = align16(off + sizeof(int16_t) * n);
     w.P = pitch_of(n);
     w.J = Jglobal ? Jglobal : reinterpret_cast<TJ *>(base + off);
+    if (!Jglobal) off = align16(off + sizeof(TJ) * size_t(n) * w.P);
+    w.tc = tc;
+    w.bar = reinterpret_cast<uint64_t *>(w.ired + 2 * kBW + 4);     // 8-byte aligned (16-aligned base)
+    w.tmem_slot = reinterpret_cast<uint32_t *>(w.ired + 2 * kBW + 6);
+    char *st = stage_in_rates(I) ? reinterpret_cast<char *>(w.kf) : base + off;
+    w.stage = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(st) + 127) & ~uintptr_t(127));
     return w;
+}
+
+// ---------------------------------------------------------------- tensor-core set-up
+// Per block, when the tensor-core update is on: warp 0 allocates the accumulator's tensor
+// memory, thread 0 initialises the mbarrier; the phase counter and the failure flag start
+// at zero. tc_end frees the tensor memory (after a bounded wait for an update that failed
+// to complete), before the block exits.
+template <class TJ>
+__device__ void tc_begin(const BWS<TJ> &w) {
+    if (!w.tc) return;
+    if (threadIdx.x < 32) tc::tmem_alloc(w.tmem_slot, tc::kTmemCols);
+    if (threadIdx.x == 0) {
+        tc::mbar_init(w.bar);
+        w.ired[2 * kBW + 1] = 0;   // phase
+        w.ired[2 * kBW + 2] = 0;   // failure
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+}
+
+template <class TJ>
+__device__ void tc_end(const BWS<TJ> &w) {
+    if (!w.tc) return;
+    __syncthreads();
+    if (w.ired[2 * kBW + 2]) tc::mbar_wait(w.bar, uint32_t((w.ired[2 * kBW + 1] - 1) & 1));   // the timed-out MMAs
+    tc::fence_after_sync();
+    if (threadIdx.x < 32) tc::tmem_dealloc(*w.tmem_slot, tc::kTmemCols);
+}
+
+// A22 -= L21 U12 on the tensor cores for the trailing matrix of a panel: rows and columns
+// [r0, n), panel columns [k0, k0 + kb). Per 128-row tile and 128-column chunk, the K = kb
+// panel width in rounds of 16: stage the TF32 tiles (hi, and lo for 3xTF32), one thread
+// issues the MMAs into the tensor-memory accumulator, all wait on the mbarrier; then each
+// warp reads its 32 accumulator lanes (rows) and subtracts them from the FP32 matrix.
+// With 3xTF32 the product is A_hi B_hi + A_hi B_lo + A_lo B_hi (FP32-like accuracy).
+// Returns false (block-uniform) when a wait timed out; the failure flag then turns the
+// tensor cores off for the rest of the launch.
+__device__ bool b_trailing_tc(const BWS<float> &w, int n, int r0, int k0, int kb) {
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int P = w.P, m = n - r0;
+    float *J = w.J;
+    const bool three = w.tc == 3;
+    char *Ah = w.stage, *Al = w.stage + 8192, *Bh = w.stage + 16384, *Bl = w.stage + 24576;
+    const uint32_t tbase = *w.tmem_slot;
+    int phase = w.ired[2 * kBW + 1];
+    bool ok = true;
+    for (int rt = 0; rt < m && ok; rt += tc::kTileM) {
+        for (int ct = 0; ct < m && ok; ct += tc::kTileM) {
+            const int cols = min(tc::kTileM, m - ct);
+            const int N = (cols + 15) & ~15;
+            for (int kh = 0; kh < kb && ok; kh += tc::kTileK) {
+                // stage L21 rows r0+rt.., panel columns k0+kh.. and U12 columns r0+ct.. (zero padded)
+                for (int e = t; e < tc::kTileM * tc::kTileK; e += kBT) {
+                    const int r = e >> 4, k = e & 15;
+                    const int gr = rt + r, gk = kh + k;
+                    const float a = (gr < m && gk < kb) ? J[size_t(r0 + gr) * P + k0 + gk] : 0.0f;
+                    const int gc = ct + r;
+                    const float b = (r < N && gc < m && gk < kb) ? J[size_t(k0 + gk) * P + r0 + gc] : 0.0f;
+                    const uint32_t o = tc::tile_off(r, k);
+                    const float ah = tc::to_tf32(a), bh = tc::to_tf32(b);
+                    *reinterpret_cast<float *>(Ah + o) = ah;
+                    *reinterpret_cast<float *>(Bh + o) = bh;
+                    if (three) {
+                        *reinterpret_cast<float *>(Al + o) = tc::to_tf32(a - ah);
+                        *reinterpret_cast<float *>(Bl + o) = tc::to_tf32(b - bh);
+                    }
+                }
+                tc::fence_async_smem();
+                __syncthreads();
+                if (t == 0) {
+                    tc::fence_after_sync();
+                    const uint32_t id = tc::idesc_tf32(tc::kTileM, N);
+                    const uint32_t sAh = tc::smem_u32(Ah), sAl = tc::smem_u32(Al), sBh = tc::smem_u32(Bh),
+                                   sBl = tc::smem_u32(Bl);
+#pragma unroll
+                    for (int s = 0; s < 2; ++s) {   // two K-steps of 8 per round
+                        const uint32_t ko = 256u * s;
+                        tc::mma_tf32(tbase, tc::smem_desc(sAh + ko), tc::smem_desc(sBh + ko), id, (kh > 0 || s > 0));
+                        if (three) {
+                            tc::mma_tf32(tbase, tc::smem_desc(sAh + ko), tc::smem_desc(sBl + ko), id, 1u);
+                            tc::mma_tf32(tbase, tc::smem_desc(sAl + ko), tc::smem_desc(sBh + ko), id, 1u);
+                        }
+                    }
+                    tc::commit(w.bar);
+                }
+                ok = __syncthreads_and(tc::mbar_wait(w.bar, uint32_t(phase & 1))) != 0;
+                ++phase;
+                tc::fence_after_sync();
+            }
+            if (ok) {
+                // epilogue: warp w reads accumulator lanes 32 (w % 4).., 16-column blocks (w / 4) * 16 + 64 u
+                const int q = wid & 3;
+                const int row = rt + 32 * q + lane;
+                for (int cb = (wid >> 2) * 16; cb < N; cb += 64) {
+                    float v[16];
+                    tc::ld16(tbase + (uint32_t(32 * q) << 16) + uint32_t(cb), v);
+                    if (row < m) {
+                        float *Jr = J + size_t(r0 + row) * P + r0 + ct + cb;
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            if (ct + cb + i < m) Jr[i] -= v[i];
+                    }
+                }
+            }
+            tc::fence_before_sync();
+            __syncthreads();
+        }
+    }
+    if (t == 0) {
+        w.ired[2 * kBW + 1] = phase;
+        if (!ok) w.ired[2 * kBW + 2] = 1;
+    }
+    __syncthreads();
+    return ok;
 }
 
 // ---------------------------------------------------------------- block reductions
@@ -471,7 +609,7 @@ struct TileRows {
 // product (8 x 4 outputs per thread, 12 shared loads per 32 FMAs). False on a zero or
 // non-finite pivot (block-uniform).
 template <class TJ>
-__device__ __noinline__ bool b_lu(const BWS<TJ> &w, int n) {
+__device__ __noinline__ bool b_lu(const BWS<TJ> &w, int n, bool tc_ok = true) {
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const int P = w.P;
     TJ *J = w.J;
@@ -568,8 +706,15 @@ __device__ __noinline__ bool b_lu(const BWS<TJ> &w, int n) {
             }
         }
         __syncthreads();
-        // A22 -= L21 U12 in chunks of (16 TA) x 128
         const int m = n - r0;
+        if constexpr (sizeof(TJ) == 4) {
+            // A22 -= L21 U12 on the tensor cores (FP32 Jacobian, large trailing matrices)
+            if (w.tc && tc_ok && m >= kTcMinM && !w.ired[2 * kBW + 2]) {
+                if (!b_trailing_tc(w, n, r0, k0, kb)) return false;
+                continue;
+            }
+        }
+        // A22 -= L21 U12 in chunks of (16 TA) x 128
         constexpr int kTA = TileRows<TJ>::value;
         for (int rb = 0; rb < m; rb += 16 * kTA) {
             for (int cb = 0; cb < m; cb += 32 * kTB) {
@@ -712,7 +857,14 @@ struct BCtx {
     int nfev;
     Mix mx;
     int K, n;
+    double fn;   // ||F||_inf of the last residual (kept only with the tensor-core LU)
 };
+
+// With the TF32 tensor-core LU (one TF32 product, 2^-11 rounding) Newton converges only
+// linearly near the root, and the polish test on the last step (which assumes fast
+// convergence) would leave minor species a few 1e-6 off: the last iterations, from
+// ||F||_inf <= kTcSwitchF on, factor on the CUDA cores in FP32.
+constexpr double kTcSwitchF = 1e-6;
 
 __device__ __forceinline__ bool b_all_finite(const double *v, int n) {
     const int t = threadIdx.x;
@@ -767,6 +919,7 @@ __device__ void b_residual_R(BCtx &cx, const BWS<TJ> &w, const double *y, const 
     b_eval_F(cx.M, w, y, F, cx.mx, cx.Yin, cx.tau, cx.P, cx.Tspec, cx.o.energy, cx.mult);
     const int t = threadIdx.x;
     if (t < cx.n) R[t] = F[t] + c[t] * (y[t] - xref[t]);
+    if (w.tc == 1) cx.fn = bmax(t < cx.n ? fabs(F[t]) : 0.0, w.red);
     __syncthreads();
 }
 
@@ -797,7 +950,7 @@ __device__ bool b_damped_newton(BCtx &cx, const BWS<TJ> &w, double *y, const dou
                 at_y = true;
             }
             b_eval_J(cx.M, w, c, cx.mx, cx.tau, o.energy, cx.mult);
-            if (!b_lu(w, n)) break;
+            if (!b_lu(w, n, cx.fn > kTcSwitchF)) break;
             have_lu = true;
             age = 0;
             fresh = true;
@@ -882,7 +1035,7 @@ __device__ bool b_linear_step(BCtx &cx, const BWS<TJ> &w, int &counter, bool &fx
     if (!fx_valid) b_residual_R(cx, w, w.x, w.c, w.x, w.F, w.R);
     fx_valid = false;   // the Jacobian consumes the rate caches
     b_eval_J(cx.M, w, w.c, cx.mx, cx.tau, o.energy, cx.mult);
-    if (!b_lu(w, n)) return false;
+    if (!b_lu(w, n, cx.fn > kTcSwitchF)) return false;
     b_lu_solve_neg(w, n, w.F, w.dy);
     if (!b_all_finite(w.dy, n)) return false;
     if (b_max_in_bounds(w.x, w.dy, K, o, w.red) < 1.0) return false;
@@ -914,8 +1067,10 @@ __device__ void b_inlet_enthalpy(BCtx &cx, double Tin, double *red) {
     cx.mx.h_in = bsum1(s, red) * kRu * Tin;
 }
 
+// Loads reactor r's inlet and starting point; returns true for a reactor a warp launch
+// handed over unfinished (it continues from the iterate left in Y_out / T_out).
 template <class TJ>
-__device__ void b_load_reactor(BCtx &cx, const BWS<TJ> &w, const Batch &bt, int64_t r) {
+__device__ bool b_load_reactor(BCtx &cx, const BWS<TJ> &w, const Batch &bt, int64_t r) {
     const int t = threadIdx.x;
     const int K = cx.K;
     const int64_t row = row_of(bt, r, K);
@@ -925,11 +1080,16 @@ __device__ void b_load_reactor(BCtx &cx, const BWS<TJ> &w, const Batch &bt, int6
     cx.Tspec = bt.T0[r];
     cx.nfev = 0;
     b_inlet_enthalpy(cx, bt.T_in[r], w.red);
+    // a reactor the warp launch handed over continues from the iterate it left in the outputs
+    const bool cont = bt.fallback && bt.status && bt.status[r] == kStatusHandoff;
+    const double *Ys = cont ? bt.Y_out : bt.Y0;
+    const double *Ts = cont ? bt.T_out : bt.T0;
     if (t < cx.n) {
-        w.x[t] = (t < K) ? bt.Y0[row + t] : bt.T0[r];
+        w.x[t] = (t < K) ? Ys[row + t] : Ts[r];
         w.c[t] = 0.0;
     }
     __syncthreads();
+    return cont;
 }
 
 template <class TJ>
@@ -937,10 +1097,13 @@ __device__ void b_solve_one(BCtx &cx, const BWS<TJ> &w, const Batch &bt, int64_t
     const int t = threadIdx.x;
     const int K = cx.K, n = cx.n;
     const Opts &o = cx.o;
-    b_load_reactor(cx, w, bt, r);
+    // a continued reactor keeps its counters (its Newton budget is the reactor's total)
+    const bool cont = b_load_reactor(cx, w, bt, r);
     const double tau = cx.tau;
+    if (cont && bt.nfev) cx.nfev = bt.nfev[r];
     b_residual_R(cx, w, w.x, w.c, w.x, w.F, w.R);
-    int status, counter = 0, ts = 0, rounds = 0;
+    int status, rounds = 0;
+    int counter = (cont && bt.iters) ? bt.iters[r] : 0, ts = (cont && bt.ts_steps) ? bt.ts_steps[r] : 0;
     const double *out = w.x;
     if (!b_all_finite(w.F, n)) {
         status = PSR_NONFINITE;
@@ -1040,12 +1203,12 @@ __device__ void b_solve_one(BCtx &cx, const BWS<TJ> &w, const Batch &bt, int64_t
     if (t < K) bt.Y_out[row_of(bt, r, K) + t] = out[t];
     if (t == 0) {
         bt.T_out[r] = out[K];
-        const bool fb = bt.fallback != 0;
-        if (bt.status) bt.status[r] = (fb && status == PSR_CONVERGED) ? PSR_REFINE_FALLBACK : status;
-        if (bt.iters) bt.iters[r] = counter + (fb ? bt.iters[r] : 0);
-        if (bt.ts_steps) bt.ts_steps[r] = ts + (fb ? bt.ts_steps[r] : 0);
+        const bool add = bt.fallback != 0 && !cont;   // a restart adds its counters to the first launch's
+        if (bt.status) bt.status[r] = (bt.fallback == 1 && status == PSR_CONVERGED) ? PSR_REFINE_FALLBACK : status;
+        if (bt.iters) bt.iters[r] = counter + (add ? bt.iters[r] : 0);
+        if (bt.ts_steps) bt.ts_steps[r] = ts + (add ? bt.ts_steps[r] : 0);
         if (bt.fnorm) bt.fnorm[r] = fn;
-        if (bt.nfev) bt.nfev[r] = cx.nfev + (fb ? bt.nfev[r] : 0);
+        if (bt.nfev) bt.nfev[r] = cx.nfev + (add ? bt.nfev[r] : 0);
     }
     __syncthreads();
 }
@@ -1053,16 +1216,19 @@ __device__ void b_solve_one(BCtx &cx, const BWS<TJ> &w, const Batch &bt, int64_t
 // ---------------------------------------------------------------- kernels
 template <class TJ>
 __global__ void __launch_bounds__(kBT, 1) block_solve_kernel(DevMech M, Batch bt, Opts o, int *queue, TJ *Jglob) {
-    extern __shared__ __align__(16) char smem[];
+    extern __shared__ __align__(128) char smem[];
     const int K = M.K, n = K + 1;
     const size_t slot = size_t(n) * pitch_of(n);
-    BWS<TJ> w = bcarve<TJ>(smem, K, M.I, M.n_troe, n, Jglob ? Jglob + blockIdx.x * slot : nullptr);
+    const int tc = (sizeof(TJ) == 4 && n >= kTcMinM + kNB) ? o.lu_tc : 0;
+    BWS<TJ> w = bcarve<TJ>(smem, K, M.I, M.n_troe, n, Jglob ? Jglob + blockIdx.x * slot : nullptr, tc);
+    tc_begin(w);
     BCtx cx;
     cx.M = M;
     cx.o = o;
     cx.mult = bt.rate_mult;
     cx.K = K;
     cx.n = n;
+    cx.fn = INFINITY;   // 3xTF32 (w.tc == 3) never switches
     const int64_t nwork = bt.list ? int64_t(*bt.list_len) : bt.B;
     while (true) {
         if (threadIdx.x == 0) w.ired[2 * kBW] = atomicAdd(queue, 1);
@@ -1073,6 +1239,7 @@ __global__ void __launch_bounds__(kBT, 1) block_solve_kernel(DevMech M, Batch bt
         const int64_t r = bt.list ? int64_t(bt.list[p]) : int64_t(p);
         b_solve_one<TJ>(cx, w, bt, r);
     }
+    tc_end(w);
 }
 
 __global__ void block_collect_unconverged(int64_t B, const int32_t *in_list, const int32_t *in_len,
@@ -1088,7 +1255,7 @@ __global__ void block_collect_unconverged(int64_t B, const int32_t *in_list, con
 template <class TJ>
 __global__ void __launch_bounds__(kBT, 1) block_eval_kernel(DevMech M, Batch bt, int energy, int want_J,
                                                             double *out, RatesOut ro, TJ *Jglob) {
-    extern __shared__ __align__(16) char smem[];
+    extern __shared__ __align__(128) char smem[];
     const int K = M.K, n = K + 1;
     const size_t slot = size_t(n) * pitch_of(n);
     BWS<TJ> w = bcarve<TJ>(smem, K, M.I, M.n_troe, n, Jglob ? Jglob + blockIdx.x * slot : nullptr);
@@ -1130,7 +1297,7 @@ __global__ void __launch_bounds__(kBT, 1) block_eval_kernel(DevMech M, Batch bt,
 __global__ void __launch_bounds__(kBT, 1) block_adjoint_kernel(DevMech M, Batch bt, int energy, const double *g,
                                                                double *grad, double *lam_out, int32_t *ok,
                                                                double *Jglob) {
-    extern __shared__ __align__(16) char smem[];
+    extern __shared__ __align__(128) char smem[];
     const int K = M.K, n = K + 1, I = M.I;
     const size_t slot = size_t(n) * pitch_of(n);
     BWS<double> w = bcarve<double>(smem, K, I, M.n_troe, n, Jglob ? Jglob + blockIdx.x * slot : nullptr);
@@ -1180,10 +1347,11 @@ __global__ void __launch_bounds__(kBT, 1) block_adjoint_kernel(DevMech M, Batch 
 
 template <class TJ>
 __global__ void __launch_bounds__(kBT, 1) block_lu_kernel(int64_t B, int n, const double *A, const double *rhs,
-                                                          double *x, int32_t *ok, TJ *Jglob) {
-    extern __shared__ __align__(16) char smem[];
+                                                          double *x, int32_t *ok, TJ *Jglob, int tc) {
+    extern __shared__ __align__(128) char smem[];
     const size_t slot = size_t(n) * pitch_of(n);
-    BWS<TJ> w = bcarve<TJ>(smem, 0, 0, 0, n, Jglob ? Jglob + blockIdx.x * slot : nullptr);
+    BWS<TJ> w = bcarve<TJ>(smem, 0, 0, 0, n, Jglob ? Jglob + blockIdx.x * slot : nullptr, tc);
+    tc_begin(w);
     const int t = threadIdx.x;
     for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
         for (int idx = t; idx < n * n; idx += kBT) w.J[size_t(idx / n) * w.P + idx % n] = TJ(A[b * n * n + idx]);
@@ -1195,6 +1363,7 @@ __global__ void __launch_bounds__(kBT, 1) block_lu_kernel(int64_t B, int n, cons
         if (t == 0) ok[b] = good ? 1 : 0;
         __syncthreads();
     }
+    tc_end(w);
 }
 
 // ---------------------------------------------------------------- host side
@@ -1207,14 +1376,14 @@ struct Launch {
 // Shared-memory plan of one block for a kernel: the Jacobian in shared memory when the
 // whole workspace fits, else in global slots (one per block).
 template <class TJ, class KernelT>
-int plan(KernelT kern, int K, int I, int nt, int n, int64_t units, int bps_req, Launch &L) {
+int plan(KernelT kern, int K, int I, int nt, int n, int64_t units, int bps_req, Launch &L, bool tc = false) {
     int dev = 0, max_smem = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const size_t with_j = bws_bytes<TJ>(K, I, nt, n, true);
+    const size_t with_j = bws_bytes<TJ>(K, I, nt, n, true, tc);
     L.j_in_smem = with_j <= size_t(max_smem);
-    L.smem = L.j_in_smem ? with_j : bws_bytes<TJ>(K, I, nt, n, false);
+    L.smem = L.j_in_smem ? with_j : bws_bytes<TJ>(K, I, nt, n, false, tc);
     if (L.smem > size_t(max_smem))
         return set_error(PSR_E_UNSUPPORTED, "mechanism tables exceed one block's shared memory");
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L.smem));
@@ -1232,7 +1401,8 @@ template <class TJ>
 int launch_block(const Mech &m, const Batch &bt, const Opts &o, int bps_req, cudaStream_t st, int *queue) {
     const int K = m.K, n = K + 1;
     Launch L;
-    int rc = plan<TJ>(block_solve_kernel<TJ>, K, m.I, m.n_troe, n, bt.B, bps_req, L);
+    const bool tc = sizeof(TJ) == 4 && n >= kTcMinM + kNB && o.lu_tc > 0;
+    int rc = plan<TJ>(block_solve_kernel<TJ>, K, m.I, m.n_troe, n, bt.B, bps_req, L, tc);
     if (rc) return rc;
     TJ *Jg = nullptr;
     cudaError_t e;
@@ -1252,11 +1422,13 @@ int launch_block(const Mech &m, const Batch &bt, const Opts &o, int bps_req, cud
 
 }  // namespace
 
-// FP64 re-solve, one block per reactor, of the reactors a warp-solver launch listed (bt.list):
-// a short list would leave the GPU almost idle under the warp solver, where one reactor
-// takes a warp for all of its iterations.
-int block_resolve_list(const Mech &m, const Batch &bt, const Opts &o, cudaStream_t st, int *queue) {
-    return launch_block<double>(m, bt, o, 0, st, queue);
+// Second launch over the reactors a warp-solver launch listed (bt.list), one block per
+// reactor, with the FP64 or the FP32 Jacobian: the mixed form's FP64 re-solve, or the
+// continuation of reactors handed over unfinished. A short list would leave the GPU almost
+// idle under the warp solver, where one reactor takes a warp for all of its iterations.
+int block_resolve_list(const Mech &m, const Batch &bt, const Opts &o, int precision, cudaStream_t st, int *queue) {
+    return precision == PSR_MIXED ? launch_block<float>(m, bt, o, 0, st, queue)
+                                  : launch_block<double>(m, bt, o, 0, st, queue);
 }
 
 int block_check(const Mech &m) {
@@ -1351,9 +1523,11 @@ int block_adjoint(const Mech &m, const Batch &bt, int energy, const double *g, d
 }
 
 template <class TJ>
-static int block_lu_t(int64_t B, int n, const double *A, const double *r, double *x, int32_t *ok, cudaStream_t st) {
+static int block_lu_t(int64_t B, int n, const double *A, const double *r, double *x, int32_t *ok, cudaStream_t st,
+                      int tc = 0) {
     Launch L;
-    int rc = plan<TJ>(block_lu_kernel<TJ>, 0, 0, 0, n, B, 0, L);
+    if (sizeof(TJ) != 4 || n < kTcMinM + kNB) tc = 0;
+    int rc = plan<TJ>(block_lu_kernel<TJ>, 0, 0, 0, n, B, 0, L, tc > 0);
     if (rc) return rc;
     TJ *Jg = nullptr;
     cudaError_t e;
@@ -1361,17 +1535,20 @@ static int block_lu_t(int64_t B, int n, const double *A, const double *r, double
         e = cudaMallocAsync(reinterpret_cast<void **>(&Jg), sizeof(TJ) * size_t(n) * pitch_of(n) * L.grid, st);
         if (e != cudaSuccess) return set_error(PSR_E_OOM, "matrix slots for the block LU");
     }
-    block_lu_kernel<TJ><<<L.grid, kBT, L.smem, st>>>(B, n, A, r, x, ok, Jg);
+    block_lu_kernel<TJ><<<L.grid, kBT, L.smem, st>>>(B, n, A, r, x, ok, Jg, tc);
     e = cudaGetLastError();
     if (Jg) cudaFreeAsync(Jg, st);
     if (e != cudaSuccess) return cuda_error("block_lu_kernel launch", e);
     return PSR_OK;
 }
 
+// precision: PSR_FP64, PSR_MIXED (FP32), or PSR_MIXED with the tensor-core trailing update
+// (lu_tc 1 = TF32, 3 = 3xTF32)
 int block_lu(int64_t B, int n, const double *A, const double *r, double *x, int32_t *ok, int precision,
-             cudaStream_t st) {
+             cudaStream_t st, int lu_tc) {
     if (n > kMaxBlockN) return set_error(PSR_E_ARG, "psr_batch_lu_solve: n > 512");
-    return precision == PSR_MIXED ? block_lu_t<float>(B, n, A, r, x, ok, st) : block_lu_t<double>(B, n, A, r, x, ok, st);
+    return precision == PSR_MIXED ? block_lu_t<float>(B, n, A, r, x, ok, st, lu_tc)
+                                  : block_lu_t<double>(B, n, A, r, x, ok, st);
 }
 
 }  // namespace psr

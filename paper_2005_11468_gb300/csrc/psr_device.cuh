@@ -69,7 +69,10 @@ struct Batch {
     double *M_out;
     const int32_t *list;       // optional work list of reactor indices (device), length *list_len
     const int32_t *list_len;
-    int fallback;              // this launch re-solves the list in FP64 after a mixed launch
+    int fallback;              // second launch over a list: 1 = FP64 re-solve after a mixed launch
+                               // (converged reactors report PSR_REFINE_FALLBACK), 2 = continuation
+                               // in the same precision; counters add up, and reactors the first
+                               // launch handed over (kStatusHandoff) start from Y_out / T_out
     const int64_t *row_off;    // optional [B] start of reactor r's row in Y_in / Y0 / Y_out (else r K)
 };
 
@@ -92,6 +95,10 @@ struct Opts {
     int mixed_max_newton;   // Newton cap of the FP32-Jacobian launch when the FP64 re-solve follows
     int jac_age;            // iterations one Jacobian factorisation may serve (1 = fresh each time)
     int ts_linear;          // linearised pseudo-time steps while the iteration count is below this
+    int handoff_pct;        // warp launch: once this percentage of its working warps found the work
+                            // queue empty, running reactors stop and go to the block solver (0 = never)
+    int lu_tc;              // block solver, FP32 Jacobian: LU trailing update on the tensor cores
+                            // (0 = CUDA cores, 1 = TF32, 3 = 3xTF32)
 };
 
 // Scalars of the last residual evaluation that the Jacobian reuses.
@@ -187,7 +194,7 @@ __device__ __forceinline__ Troe troe_eval(const double *__restrict__ tp, double 
 // Host launchers of the block-per-reactor solver (psr_block.cu), for mechanisms whose
 // K + 1 unknowns exceed one warp's 64.
 int block_check(const Mech &m);
-int block_resolve_list(const Mech &m, const Batch &bt, const Opts &o, cudaStream_t st, int *queue);
+int block_resolve_list(const Mech &m, const Batch &bt, const Opts &o, int precision, cudaStream_t st, int *queue);
 int block_solve(const Mech &m, const Batch &bt, const Opts &o, int precision, bool fallback, int bps_req,
                 cudaStream_t st);
 int block_eval(const Mech &m, const Batch &bt, int energy, int want_J, int precision, double *out, cudaStream_t st,
@@ -195,6 +202,6 @@ int block_eval(const Mech &m, const Batch &bt, int energy, int want_J, int preci
 int block_adjoint(const Mech &m, const Batch &bt, int energy, const double *g, double *grad, double *lam_out,
                   int32_t *ok, cudaStream_t st);
 int block_lu(int64_t B, int n, const double *A, const double *r, double *x, int32_t *ok, int precision,
-             cudaStream_t st);
+             cudaStream_t st, int lu_tc = 0);
 
 }  // namespace psr

@@ -18,6 +18,11 @@ constexpr int64_t kMaxBatch = (int64_t(1) << 31) - (int64_t(1) << 22);
 
 enum RxnType : int8_t { kElem = 0, kThirdBody = 1, kTroe = 2 };
 
+// Per-reactor status between the two launches of a solve (never returned to the caller):
+// the warp launch handed the unfinished reactor over to the block solver, which continues
+// it from the iterate left in Y_out / T_out.
+constexpr int32_t kStatusHandoff = 8;
+
 // Device-side view of a mechanism: structure-of-arrays tables, all device pointers.
 struct DevMech {
     int K, I, n_troe, n_eff;
@@ -25,6 +30,7 @@ struct DevMech {
     const float *invW_f;         // [K] 1/W in FP32 (the FP32 Jacobian's transform)
     const double *nasa;          // [K][16]: T_mid, low a1..a7, high a1..a7, 0
     const double *lnA, *beta, *theta;   // [I] Eq. (6), E/R in K
+    const float *beta_f, *theta_f;      // [I] the same in FP32 (the FP32 Jacobian's rate derivatives)
     const int16_t *slots;        // [I][6] reactant slots 0..2, product slots 3..5, K = empty
     const int8_t *dnu;           // [I] sum_k nu_ki
     const double *dnu_d;         // [I] the same as double

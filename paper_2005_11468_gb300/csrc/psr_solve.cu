@@ -20,14 +20,17 @@
 namespace psr {
 namespace {
 
-// Work list of the reactors a mixed-precision launch left unconverged (among in_list
-// when given, else among all B).
+// Work list for the second launch of a solve (among in_list when given, else among all B):
+// every reactor the first launch left unconverged (handoff_only = 0, the mixed form's FP64
+// re-solve), or only those it handed over unfinished (handoff_only = 1, a continuation in
+// the same precision).
 __global__ void collect_unconverged(int64_t B, const int32_t *in_list, const int32_t *in_len, const int32_t *status,
-                                    int32_t *list, int32_t *len) {
+                                    int32_t *list, int32_t *len, int handoff_only) {
     const int64_t n = in_list ? int64_t(*in_len) : B;
     for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < n; p += int64_t(gridDim.x) * blockDim.x) {
         const int64_t r = in_list ? int64_t(in_list[p]) : p;
-        if (status[r] != PSR_CONVERGED) list[atomicAdd(len, 1)] = int32_t(r);
+        const bool take = handoff_only ? status[r] == kStatusHandoff : status[r] != PSR_CONVERGED;
+        if (take) list[atomicAdd(len, 1)] = int32_t(r);
     }
 }
 
@@ -304,6 +307,10 @@ Opts to_opts(const psr_options *po) {
     o.jac_age = s.jac_age < 1 ? 1 : s.jac_age;
     o.ts_linear = s.ts_linear;
     o.energy = s.energy;
+    // handoff by default where it was measured to pay: the FP64 form (at K = 53 the block
+    // solver finishes a straggler ~1.6x sooner than a warp with the FP64 LU, ~1.3x with FP32)
+    o.handoff_pct = s.handoff >= 0 ? s.handoff : (s.precision == PSR_FP64 ? 75 : 0);
+    o.lu_tc = s.lu_tensor;
     return o;
 }
 
@@ -318,7 +325,8 @@ int check_opts(const psr_options *po) {
         (s.energy != PSR_ADIABATIC && s.energy != PSR_FIXED_T) || s.warps_per_block < 0 || s.warps_per_block > 32 ||
         s.blocks_per_sm < 0 || (s.mixed_fallback != 0 && s.mixed_fallback != 1) ||
         (s.jacobian != PSR_JAC_ANALYTIC && s.jacobian != PSR_JAC_FD) || s.mixed_max_newton < 0 || s.jac_age < 0 ||
-        s.jac_age > 64 || s.ts_linear < 0 || s.path < PSR_PATH_AUTO || s.path > PSR_PATH_BLOCK)
+        s.jac_age > 64 || s.ts_linear < 0 || s.path < PSR_PATH_AUTO || s.path > PSR_PATH_BLOCK || s.handoff < -1 ||
+        s.handoff > 100 || (s.lu_tensor != PSR_LU_CUDA_CORES && s.lu_tensor != PSR_LU_TF32 && s.lu_tensor != PSR_LU_3XTF32))
         return set_error(PSR_E_ARG, "psr_options: value out of range");
     return PSR_OK;
 }
@@ -359,7 +367,7 @@ int launch_solve_qs(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, 
     int64_t want = (bt.B + wpb - 1) / wpb;
     int64_t grid = std::min<int64_t>(int64_t(per_sm) * nsm, want);
     if (grid < 1) grid = 1;
-    e = cudaMemsetAsync(queue, 0, sizeof(int), st);
+    e = cudaMemsetAsync(queue, 0, 2 * sizeof(int), st);
     if (e != cudaSuccess) return cuda_error("cudaMemsetAsync(work queue)", e);
     e = launch_solve_kernel<TJ, SOOT, FDJ>(unsigned(grid), wpb * 32, smem, st, m.dev, bt, o, queue, wsb);
     if (e != cudaSuccess) return cuda_error("solve_kernel launch", e);
@@ -376,13 +384,58 @@ int launch_solve_q(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, i
     return launch_solve_qs<TJ, false>(m, bt, o, wpb_req, bps_req, st, queue);
 }
 
+// Reactors the warp launch hands over unfinished can continue on the block solver: gas
+// mechanisms that fit it, with the analytic Jacobian (the block solver has no other).
+bool can_hand_over(const Mech &m, const Opts &o) {
+    return o.handoff_pct > 0 && !m.dev.nsoot && !o.jac_fd && block_check(m) == PSR_OK;
+}
+
+// One warp per reactor in the Jacobian precision TJ. With handoff enabled, the reactors
+// the warp launch hands over once its queue has drained and most warps are idle continue
+// from their iterates on the block solver in the same precision (a device-side list, no
+// host synchronisation): the stragglers get a thread block each instead of one warp.
 template <class TJ>
 int launch_solve(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int bps_req, cudaStream_t st) {
-    int *queue = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&queue), sizeof(int), st);
-    if (e != cudaSuccess) return set_error(PSR_E_OOM, "work-queue allocation failed");
-    const int rc = launch_solve_q<TJ>(m, bt, o, wpb_req, bps_req, st, queue);
-    cudaFreeAsync(queue, st);
+    if (!can_hand_over(m, o)) {
+        int *queue = nullptr;
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&queue), 2 * sizeof(int), st);
+        if (e != cudaSuccess) return set_error(PSR_E_OOM, "work-queue allocation failed");
+        Opts o1 = o;
+        o1.handoff_pct = 0;
+        const int rc = launch_solve_q<TJ>(m, bt, o1, wpb_req, bps_req, st, queue);
+        cudaFreeAsync(queue, st);
+        return rc;
+    }
+    const size_t B = size_t(bt.B);
+    int32_t *scr = nullptr;
+    // queues, list length, the list, and status / iteration counts when the caller passed none
+    // (the second launch reads both)
+    const size_t n_ints = 8 + B + (bt.status ? 0 : B) + (bt.iters ? 0 : B);
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scr), n_ints * sizeof(int32_t), st);
+    if (e != cudaSuccess) return set_error(PSR_E_OOM, "scratch allocation failed");
+    int32_t *q0 = scr, *q1 = scr + 2, *len = scr + 4, *list = scr + 8, *extra = scr + 8 + B;
+    Batch b1 = bt;
+    if (!bt.status) {
+        b1.status = extra;
+        extra += B;
+    }
+    if (!bt.iters) b1.iters = extra;
+    int rc = launch_solve_q<TJ>(m, b1, o, wpb_req, bps_req, st, q0);
+    if (rc == PSR_OK) {
+        cudaMemsetAsync(len, 0, sizeof(int32_t), st);
+        collect_unconverged<<<unsigned((B + 255) / 256), 256, 0, st>>>(bt.B, bt.list, bt.list_len, b1.status, list,
+                                                                       len, 1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_error("collect_unconverged launch", e);
+    }
+    if (rc == PSR_OK) {
+        Batch b2 = b1;
+        b2.list = list;
+        b2.list_len = len;
+        b2.fallback = 2;
+        rc = block_resolve_list(m, b2, o, sizeof(TJ) == 8 ? PSR_FP64 : PSR_MIXED, st, q1);
+    }
+    cudaFreeAsync(scr, st);
     return rc;
 }
 
@@ -397,23 +450,52 @@ Opts mixed_first(const Opts &o) {
 // Mixed form with per-reactor FP64 fallback: the FP32-Jacobian launch, then the reactors
 // it left unconverged (a device-side list, no host synchronisation) solved again from
 // their initial guesses with the FP64 Jacobian; those that converge get
-// PSR_REFINE_FALLBACK and their iteration counts add up.
+// PSR_REFINE_FALLBACK and their iteration counts add up. Reactors the first launch handed
+// over unfinished (handoff) are in the same list and continue from their iterates.
 int launch_mixed(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int bps_req, bool fallback,
                  cudaStream_t st) {
     if (!fallback) return launch_solve<float>(m, bt, o, wpb_req, bps_req, st);
     const size_t B = size_t(bt.B);
     int32_t *scr = nullptr;
-    const size_t n_ints = 4 + B + (bt.status ? 0 : B);
+    // queues, list length, the list, and status / iteration counts when the caller passed none
+    // (the second launch reads both)
+    const size_t n_ints = 8 + B + (bt.status ? 0 : B) + (bt.iters ? 0 : B);
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scr), n_ints * sizeof(int32_t), st);
     if (e != cudaSuccess) return set_error(PSR_E_OOM, "scratch allocation failed");
-    int32_t *q0 = scr, *q1 = scr + 1, *len = scr + 2, *list = scr + 4;
+    int32_t *q0 = scr, *q1 = scr + 2, *len = scr + 4, *list = scr + 8, *extra = scr + 8 + B;
     Batch b1 = bt;
-    if (!bt.status) b1.status = scr + 4 + B;
-    int rc = launch_solve_q<float>(m, b1, mixed_first(o), wpb_req, bps_req, st, q0);
+    if (!bt.status) {
+        b1.status = extra;
+        extra += B;
+    }
+    if (!bt.iters) b1.iters = extra;
+    Opts o1 = mixed_first(o);
+    // the re-solve of gas-phase reactors runs on the block solver, which can also continue
+    // the reactors the warp launch hands over
+    const bool block_fb = !m.dev.nsoot && block_check(m) == PSR_OK;
+    const bool hand = block_fb && can_hand_over(m, o);
+    if (!hand) o1.handoff_pct = 0;
+    int rc = launch_solve_q<float>(m, b1, o1, wpb_req, bps_req, st, q0);
+    if (rc == PSR_OK && hand) {
+        // handed-over reactors continue with the FP32 Jacobian on the block solver (same
+        // cap as the warp launch); whatever that leaves unconverged joins the FP64 list
+        cudaMemsetAsync(len, 0, sizeof(int32_t), st);
+        collect_unconverged<<<unsigned((B + 255) / 256), 256, 0, st>>>(bt.B, bt.list, bt.list_len, b1.status, list,
+                                                                       len, 1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_error("collect_unconverged launch", e);
+        if (rc == PSR_OK) {
+            Batch bc = b1;
+            bc.list = list;
+            bc.list_len = len;
+            bc.fallback = 2;
+            rc = block_resolve_list(m, bc, o1, PSR_MIXED, st, q1);
+        }
+    }
     if (rc == PSR_OK) {
         cudaMemsetAsync(len, 0, sizeof(int32_t), st);
         collect_unconverged<<<unsigned((B + 255) / 256), 256, 0, st>>>(bt.B, bt.list, bt.list_len, b1.status, list,
-                                                                       len);
+                                                                       len, 0);
         e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_error("collect_unconverged launch", e);
     }
@@ -423,8 +505,8 @@ int launch_mixed(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int
         b2.list_len = len;
         b2.fallback = 1;
         // the list is short: gas-phase reactors go to the block solver, one CTA each
-        if (!m.dev.nsoot && block_check(m) == PSR_OK)
-            rc = block_resolve_list(m, b2, o, st, q1);
+        if (block_fb)
+            rc = block_resolve_list(m, b2, o, PSR_FP64, st, q1);
         else
             rc = launch_solve_q<double>(m, b2, o, wpb_req, bps_req, st, q1);
     }
@@ -495,7 +577,9 @@ int launch_solve_noalloc(const Mech &m, const Batch &bt, const Opts &o, int wpb_
     int32_t *queue = nullptr;
     const int rc = noalloc_scratch(&queue);
     if (rc != PSR_OK) return rc;
-    return launch_solve_q<TJ>(m, bt, o, wpb_req, bps_req, st, queue);
+    Opts o1 = o;
+    o1.handoff_pct = 0;   // a continuation launch would need an allocated work list
+    return launch_solve_q<TJ>(m, bt, o1, wpb_req, bps_req, st, queue);
 }
 
 // Mechanisms with at most 64 unknowns run on the warp-per-reactor kernels, larger gas
@@ -823,6 +907,18 @@ int psr_batch_lu_solve(int64_t B, int32_t n, const double *A, const double *r, d
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error("lu_kernel launch", e);
     return PSR_OK;
+}
+
+int psr_batch_lu_solve_tc(int64_t B, int32_t n, const double *A, const double *r, double *x_out, int32_t *ok_out,
+                          int32_t lu_tensor, void *cuda_stream) {
+    if (lu_tensor != PSR_LU_CUDA_CORES && lu_tensor != PSR_LU_TF32 && lu_tensor != PSR_LU_3XTF32)
+        return set_error(PSR_E_ARG, "psr_batch_lu_solve_tc: lu_tensor must be PSR_LU_CUDA_CORES, _TF32 or _3XTF32");
+    if (n <= kMaxWarpN || lu_tensor == PSR_LU_CUDA_CORES)
+        return psr_batch_lu_solve(B, n, A, r, x_out, ok_out, PSR_MIXED, cuda_stream);
+    if (B < 0 || B > kMaxBatch || n > 512) return set_error(PSR_E_ARG, "psr_batch_lu_solve_tc: bad B or n");
+    if (B == 0) return PSR_OK;
+    if (!A || !r || !x_out || !ok_out) return set_error(PSR_E_ARG, "psr_batch_lu_solve_tc: NULL pointer");
+    return block_lu(B, n, A, r, x_out, ok_out, PSR_MIXED, static_cast<cudaStream_t>(cuda_stream), lu_tensor);
 }
 
 int psr_batch_solve_multi(const psr_mech *const *mechs, int32_t n_mech, int64_t B, const int32_t *mech_id,

@@ -56,6 +56,12 @@ namespace {
 #ifndef PSR_STAGE_SOLVE
 #define PSR_STAGE_SOLVE PSR_STAGE
 #endif
+#ifndef PSR_STAGE_RES
+#define PSR_STAGE_RES
+#endif
+#ifndef PSR_STAGE_NEWTON
+#define PSR_STAGE_NEWTON
+#endif
 // A length-n vector distributed over the warp: lane l holds components l and l + 32.
 struct V2 {
     double a, b;
@@ -77,6 +83,8 @@ struct WS {
     TJ *rhs;                 // [n]
     int16_t *perm;           // [n] row order after pivoting
     int P;                   // row pitch of J (elements)
+    // FP32 Jacobian only: FP32 copies of C and H/RT [K+1] and the dense third-body part [K]
+    float *Cf, *hf, *vf;
 };
 
 constexpr int kSootFD = 17 * 7 + 7 * 8;   // doubles of the soot finite-difference scratch
@@ -89,6 +97,8 @@ __host__ __device__ inline size_t ws_bytes(int K, int I, int n, int nt, int ns =
     b += sizeof(TJ) * (size_t(n) * P + n);
     b = (b + 15) & ~size_t(15);
     b += sizeof(int16_t) * n;
+    b = (b + 15) & ~size_t(15);
+    if (sizeof(TJ) == 4) b += sizeof(float) * (3 * K + 2);
     return (b + 15) & ~size_t(15);
 }
 
@@ -114,6 +124,15 @@ __device__ WS<TJ> carve(char *base, int K, int I, int n, int nt, int ns = 0) {
     off += sizeof(TJ) * (size_t(n) * w.P + n);
     off = (off + 15) & ~size_t(15);
     w.perm = reinterpret_cast<int16_t *>(base + off);
+    off += sizeof(int16_t) * n;
+    off = (off + 15) & ~size_t(15);
+    if (sizeof(TJ) == 4) {
+        w.Cf = reinterpret_cast<float *>(base + off);
+        w.hf = w.Cf + (K + 1);
+        w.vf = w.hf + (K + 1);
+    } else {
+        w.Cf = w.hf = w.vf = nullptr;
+    }
     return w;
 }
 
@@ -422,6 +441,124 @@ __device__ PSR_STAGE_F void eval_F(const DevMech &M, const WS<TJ> &w, const V2 &
 }
 
 // ---------------------------------------------------------------- Jacobian
+// Per-reaction pieces of the concentration Jacobian, lanes over reactions, in the
+// arithmetic type TA (FP64, or FP32 for the FP32 Jacobian, where the pieces only steer
+// Newton and FP64 instructions are the scarce resource): d q_i / d[X_l] for each distinct
+// participant l scattered as nu_ki d q_i / d[X_l] into J (shared-memory atomics in TJ),
+// the third-body part d q_i / d[M] into the dense per-row vector vd (every column) and
+// the efficiency corrections; q_i and kf_i are replaced by the reaction's Euler sum
+// g_i = sum_l [X_l] d q_i / d[X_l] and its T-derivative d q_i / dT.
+template <class TA>
+__device__ __forceinline__ TA slot_deriv_t(int m, TA d0, TA d1, TA d2) {
+    const TA first = (m & 1) ? d0 : ((m & 2) ? d1 : ((m & 4) ? d2 : TA(0)));
+    const int rest = m & (m - 1);
+    TA v = first + ((rest & 2) ? d1 : ((rest & 4) ? d2 : TA(0)));
+    if (m == 7) v += d2;
+    return v;
+}
+template <class TA>
+__device__ __forceinline__ TA beta_v(const DevMech &M, int i);
+template <>
+__device__ __forceinline__ double beta_v<double>(const DevMech &M, int i) { return __ldg(M.beta + i); }
+template <>
+__device__ __forceinline__ float beta_v<float>(const DevMech &M, int i) { return __ldg(M.beta_f + i); }
+template <class TA>
+__device__ __forceinline__ TA theta_v(const DevMech &M, int i);
+template <>
+__device__ __forceinline__ double theta_v<double>(const DevMech &M, int i) { return __ldg(M.theta + i); }
+template <>
+__device__ __forceinline__ float theta_v<float>(const DevMech &M, int i) { return __ldg(M.theta_f + i); }
+template <class TA>
+__device__ __forceinline__ TA dnu_v(const DevMech &M, int i) {
+    if constexpr (sizeof(TA) == 8) return __ldg(M.dnu_d + i);
+    else return TA(__ldg(M.dnu + i));
+}
+
+template <class TJ, class TA>
+__device__ __forceinline__ void jac_reactions(const DevMech &M, const WS<TJ> &w, const Mix &mx,
+                                              const double *__restrict__ mult, const TA *C, const TA *hRT,
+                                              TA *vd) {
+    const int lane = threadIdx.x & 31;
+    const int K = M.K, I = M.I, P = w.P;
+    const TA invT = TA(mx.invT), Ctot = TA(mx.Ctot);
+    for (int i = lane; i < I; i += 32) {
+        const int16_t *sl6 = M.slots + size_t(i) * 6;
+        int s[6];
+        TA cs[6];
+#pragma unroll
+        for (int t = 0; t < 6; ++t) {
+            s[t] = __ldg(sl6 + t);
+            cs[t] = C[s[t]];
+        }
+        const TA Pf = cs[0] * cs[1] * cs[2], Pr_ = cs[3] * cs[4] * cs[5];
+        const TA d0 = cs[1] * cs[2], d1 = cs[0] * cs[2], d2 = cs[0] * cs[1];
+        const TA d3 = cs[4] * cs[5], d4 = cs[3] * cs[5], d5 = cs[3] * cs[4];
+        const TA kf = TA(w.kf[i]), kr = TA(w.kr[i]);
+        const TA m = mult ? TA(__ldg(mult + __ldg(M.orig + i))) : TA(1);
+        const int typ = __ldg(M.type + i);
+        TA Mc = TA(1);
+        if (typ != kElem) {
+            Mc = Ctot;
+            for (int e = __ldg(M.eff_ptr + i); e < __ldg(M.eff_ptr + i + 1); ++e)
+                Mc += eff_v<TA>(M, e) * C[__ldg(M.eff_sp + e)];
+        }
+        const TA sM = (typ == kThirdBody) ? Mc : TA(1);
+        const TA dlkf = beta_v<TA>(M, i) * invT + theta_v<TA>(M, i) * invT * invT;
+        const TA dlKc = ((hRT[s[3]] + hRT[s[4]] + hRT[s[5]]) - (hRT[s[0]] + hRT[s[1]] + hRT[s[2]]) - dnu_v<TA>(M, i)) *
+                        invT;
+        TA dlkfe = dlkf, dqdM = TA(0);
+        if (typ == kThirdBody) {
+            dqdM = m * (kf * Pf - kr * Pr_);
+        } else if (typ == kTroe) {
+            const int tr = __ldg(M.troe_row + i);
+            dlkfe = dlkf + TA(w.tX[tr]);
+            dqdM = m * (kf * Pf - kr * Pr_) * TA(w.tD[tr]) / Mc;
+        }
+        const TA dlkre = dlkfe - dlKc;
+        const TA Af = m * sM * kf, Ar = m * sM * kr;
+        const int nf = (s[0] < K) + (s[1] < K) + (s[2] < K), nr = (s[3] < K) + (s[4] < K) + (s[5] < K);
+        TA g = Af * TA(nf) * Pf - Ar * TA(nr) * Pr_;
+        if (typ != kElem) g += dqdM * Mc;
+        const TA dqdT = Af * Pf * dlkfe - Ar * Pr_ * dlkre;
+        // d q / d[X_l] for each distinct participant from its slot masks
+        const int16_t *pp = M.part + size_t(i) * 6;
+        const int8_t *pn = M.part_nu + size_t(i) * 6;
+        const int8_t *pfm = M.part_fm + size_t(i) * 6;
+        const int8_t *prm = M.part_rm + size_t(i) * 6;
+        int pl[6];
+        TJ pnu[6], val[6];
+#pragma unroll
+        for (int t = 0; t < 6; ++t) {
+            pl[t] = __ldg(pp + t);
+            pnu[t] = TJ(__ldg(pn + t));
+            const int fm = __ldg(pfm + t), rm = __ldg(prm + t);
+            const TA dfl = slot_deriv_t<TA>(fm, d0, d1, d2);
+            const TA drl = slot_deriv_t<TA>(rm, d3, d4, d5);
+            val[t] = TJ(Af * dfl - Ar * drl);
+        }
+        const TJ dqdM_t = TJ(dqdM);
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+            if (pl[r] >= K || pnu[r] == TJ(0)) continue;
+            TJ *row = w.J + size_t(pl[r]) * P;
+#pragma unroll
+            for (int t = 0; t < 6; ++t) {
+                if (pl[t] >= K) continue;
+                atomicAdd(row + pl[t], pnu[r] * val[t]);
+            }
+            if (typ != kElem) {
+                atomicAdd(vd + pl[r], TA(pnu[r]) * dqdM);
+                for (int e = __ldg(M.eff_ptr + i); e < __ldg(M.eff_ptr + i + 1); ++e)
+                    atomicAdd(row + __ldg(M.eff_sp + e), pnu[r] * dqdM_t * eff_v<TJ>(M, e));
+            }
+        }
+        // per-reaction Euler sum and T-derivative replace q and kf (read by this lane only)
+        w.q[i] = double(g);
+        w.kf[i] = double(dqdT);
+    }
+}
+
+// ---------------------------------------------------------------- Jacobian
 // Analytic dF/dx at the state of the last eval_F (whose C, hRT, kf, kr, troe cache,
 // v = wdot and mx/sl it reuses), plus diag(c), written into w.J (rows/cols 0..n-1).
 // Chain: concentration Jacobian Jc = d wdot / d[X] (per-reaction sparse blocks, a dense
@@ -442,83 +579,20 @@ __device__ PSR_STAGE_J void eval_J(const DevMech &M, const WS<TJ> &w, const V2 &
     }
     __syncwarp();
     for (int idx = lane; idx < n * P; idx += 32) w.J[idx] = TJ(0);
-    for (int j = lane; j < K; j += 32) w.v[j] = 0.0;
-    __syncwarp();
     const double T = mx.T, invT = mx.invT;
-    for (int i = lane; i < I; i += 32) {
-        const int16_t *sl6 = M.slots + size_t(i) * 6;
-        int s[6];
-        double cs[6];
-#pragma unroll
-        for (int t = 0; t < 6; ++t) {
-            s[t] = __ldg(sl6 + t);
-            cs[t] = w.C[s[t]];
+    if constexpr (sizeof(TJ) == 4) {
+        // FP32 Jacobian: FP32 copies of C and H/RT, the dense part accumulated in FP32
+        for (int j = lane; j <= K; j += 32) {
+            w.Cf[j] = float(w.C[j]);
+            w.hf[j] = float(w.hRT[j]);
+            if (j < K) w.vf[j] = 0.0f;
         }
-        const double Pf = cs[0] * cs[1] * cs[2], Pr_ = cs[3] * cs[4] * cs[5];
-        const double d0 = cs[1] * cs[2], d1 = cs[0] * cs[2], d2 = cs[0] * cs[1];
-        const double d3 = cs[4] * cs[5], d4 = cs[3] * cs[5], d5 = cs[3] * cs[4];
-        const double kf = w.kf[i], kr = w.kr[i];
-        const double m = mult ? __ldg(mult + __ldg(M.orig + i)) : 1.0;
-        const int typ = __ldg(M.type + i);
-        double Mc = 1.0;
-        if (typ != kElem) {
-            Mc = mx.Ctot;
-            for (int e = __ldg(M.eff_ptr + i); e < __ldg(M.eff_ptr + i + 1); ++e)
-                Mc += __ldg(M.eff_val + e) * w.C[__ldg(M.eff_sp + e)];
-        }
-        const double sM = (typ == kThirdBody) ? Mc : 1.0;
-        const double dlkf = __ldg(M.beta + i) * invT + __ldg(M.theta + i) * invT * invT;
-        const double dlKc = ((w.hRT[s[3]] + w.hRT[s[4]] + w.hRT[s[5]]) - (w.hRT[s[0]] + w.hRT[s[1]] + w.hRT[s[2]]) -
-                             __ldg(M.dnu_d + i)) * invT;
-        double dlkfe = dlkf, dqdM = 0.0;
-        if (typ == kThirdBody) {
-            dqdM = m * (kf * Pf - kr * Pr_);
-        } else if (typ == kTroe) {
-            const int tr = __ldg(M.troe_row + i);
-            dlkfe = dlkf + w.tX[tr];
-            dqdM = m * (kf * Pf - kr * Pr_) * w.tD[tr] / Mc;
-        }
-        const double dlkre = dlkfe - dlKc;
-        const double Af = m * sM * kf, Ar = m * sM * kr;
-        const int nf = (s[0] < K) + (s[1] < K) + (s[2] < K), nr = (s[3] < K) + (s[4] < K) + (s[5] < K);
-        double g = Af * nf * Pf - Ar * nr * Pr_;
-        if (typ != kElem) g += dqdM * Mc;
-        const double dqdT = Af * Pf * dlkfe - Ar * Pr_ * dlkre;
-        // d q / d[X_l] for each distinct participant from its slot masks
-        const int16_t *pp = M.part + size_t(i) * 6;
-        const int8_t *pn = M.part_nu + size_t(i) * 6;
-        const int8_t *pfm = M.part_fm + size_t(i) * 6;
-        const int8_t *prm = M.part_rm + size_t(i) * 6;
-        int pl[6];
-        TJ pnu[6], val[6];
-#pragma unroll
-        for (int t = 0; t < 6; ++t) {
-            pl[t] = __ldg(pp + t);
-            pnu[t] = TJ(__ldg(pn + t));
-            const int fm = __ldg(pfm + t), rm = __ldg(prm + t);
-            const double dfl = slot_deriv(fm, d0, d1, d2);
-            const double drl = slot_deriv(rm, d3, d4, d5);
-            val[t] = TJ(Af * dfl - Ar * drl);
-        }
-        const TJ dqdM_t = TJ(dqdM);
-#pragma unroll
-        for (int r = 0; r < 6; ++r) {
-            if (pl[r] >= K || pnu[r] == TJ(0)) continue;
-            TJ *row = w.J + size_t(pl[r]) * P;
-#pragma unroll
-            for (int t = 0; t < 6; ++t) {
-                if (pl[t] >= K) continue;
-                atomicAdd(row + pl[t], pnu[r] * val[t]);
-            }
-            if (typ != kElem) {
-                atomicAdd(w.v + pl[r], double(pnu[r]) * dqdM);
-                for (int e = __ldg(M.eff_ptr + i); e < __ldg(M.eff_ptr + i + 1); ++e)
-                    atomicAdd(row + __ldg(M.eff_sp + e), pnu[r] * dqdM_t * eff_v<TJ>(M, e));
-            }
-        }
-        // per-reaction Euler sum and T-derivative replace q and kf (read by this lane only)
-        w.q[i] = g;
-        w.kf[i] = dqdT;
+        __syncwarp();
+        jac_reactions<TJ, float>(M, w, mx, mult, w.Cf, w.hf, w.vf);
+    } else {
+        for (int j = lane; j < K; j += 32) w.v[j] = 0.0;
+        __syncwarp();
+        jac_reactions<TJ, double>(M, w, mx, mult, w.C, w.hRT, w.v);
     }
     __syncwarp();
     // species sums s_k = sum_i nu_ki g_i, wT_k = sum_i nu_ki dq_i/dT
@@ -535,7 +609,8 @@ __device__ PSR_STAGE_J void eval_J(const DevMech &M, const WS<TJ> &w, const V2 &
             }
             sk[h] = a;
             wT[h] = b;
-            vk[h] = w.v[j];
+            if constexpr (sizeof(TJ) == 4) vk[h] = double(w.vf[j]);
+            else vk[h] = w.v[j];
         }
     }
     const double rho = mx.rho, Wbar = mx.Wbar, RT = kRu * T;
@@ -968,10 +1043,26 @@ struct Ctx {
     Mix mx;
     SpecLane sl;
     int K, n;
+    const int *idle;   // warps of this launch that found the work queue empty
+    int handoff_at;    // idle count at which running reactors are handed over (0 = never)
+    bool handoff;      // set once this reactor is to be handed to the block solver
 };
 
+// True once enough warps of the launch are idle that the reactor this warp is solving
+// goes to the block solver (one thread block per reactor finishes a straggler far sooner
+// than a lone warp): checked at each Newton iteration, one global load by lane 0.
+__device__ __forceinline__ bool handoff_due(Ctx &cx) {
+    if (cx.handoff_at <= 0) return false;
+    int v = 0;
+    if ((threadIdx.x & 31) == 0) v = *reinterpret_cast<const volatile int *>(cx.idle);
+    v = __shfl_sync(kFull, v, 0);
+    cx.handoff = v >= cx.handoff_at;
+    return cx.handoff;
+}
+
 template <class TJ, bool SOOT>
-__device__ void residual_R(Ctx &cx, const WS<TJ> &w, const V2 &y, const V2 &c, const V2 &xref, V2 &F, V2 &R) {
+__device__ PSR_STAGE_RES void residual_R(Ctx &cx, const WS<TJ> &w, const V2 &y, const V2 &c, const V2 &xref, V2 &F,
+                                         V2 &R) {
     ++cx.nfev;
     eval_F<TJ, SOOT>(cx.M, w, y, F, cx.mx, cx.sl, cx.r.Yin, cx.r.Min, cx.r.tau, cx.r.P, cx.r.Tspec, cx.o.energy,
                      cx.mult);
@@ -981,7 +1072,7 @@ __device__ void residual_R(Ctx &cx, const WS<TJ> &w, const V2 &y, const V2 &c, c
 
 // Damped Newton on R(y) = F(y) + c (y - xref) from y (see the oracle's description).
 template <class TJ, bool SOOT, bool FDJ = false>
-__device__ bool damped_newton(Ctx &cx, const WS<TJ> &w, V2 &y, const V2 &xref, const V2 &c, int max_it,
+__device__ PSR_STAGE_NEWTON bool damped_newton(Ctx &cx, const WS<TJ> &w, V2 &y, const V2 &xref, const V2 &c, int max_it,
                               bool steady, int &counter, double *fnorm) {
     const int K = cx.K, n = cx.n;
     const Opts &o = cx.o;
@@ -995,7 +1086,7 @@ __device__ bool damped_newton(Ctx &cx, const WS<TJ> &w, V2 &y, const V2 &xref, c
     bool have_lu = false, at_y = true;
     int age = 0;
     for (int it = 0; it < max_it; ++it) {
-        if (counter >= o.max_newton) break;
+        if (counter >= o.max_newton || handoff_due(cx)) break;
         ++counter;
         bool fresh = false;
         if (!have_lu || age + 1 >= o.jac_age) {
@@ -1090,7 +1181,7 @@ __device__ bool linear_step(Ctx &cx, const WS<TJ> &w, V2 &x, V2 &Fx, bool &fx_va
                             double &f_new) {
     const int K = cx.K, n = cx.n;
     const Opts &o = cx.o;
-    if (counter >= o.max_newton) return false;
+    if (counter >= o.max_newton || handoff_due(cx)) return false;
     ++counter;
     const V2 zero{0.0, 0.0};
     if (!fx_valid) {
@@ -1173,6 +1264,7 @@ __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) 
     cx.r.P = bt.P[r];
     cx.r.Tspec = bt.T0[r];
     cx.nfev = 0;
+    cx.handoff = false;
     // inlet enthalpy sum_k Y_k,in h_k(T_in)
     {
         const double Tin = bt.T_in[r], lnTin = log(Tin);
@@ -1206,6 +1298,11 @@ __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) 
             bool conv = damped_newton<TJ, SOOT, FDJ>(cx, w, y, x, zero, o.max_newton, true, counter, fn);
             if (conv) {
                 status = PSR_CONVERGED;
+                out = y;
+                break;
+            }
+            if (cx.handoff) {   // the Newton iterate is no worse than x (monotone corrections)
+                status = kStatusHandoff;
                 out = y;
                 break;
             }
@@ -1245,6 +1342,12 @@ __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) 
                     f_new = fs[1];
                 }
                 const int used = counter - used0;
+                if (cx.handoff) {   // the last accepted pseudo-time state
+                    status = kStatusHandoff;
+                    out = x;
+                    done = true;
+                    break;
+                }
                 if (counter >= o.max_newton) {
                     status = PSR_MAX_ITER;
                     out = x;
@@ -1294,7 +1397,7 @@ __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) 
     if (lane == 0) {
         bt.T_out[r] = Tout;
         const bool fb = bt.fallback != 0;
-        if (bt.status) bt.status[r] = (fb && status == PSR_CONVERGED) ? PSR_REFINE_FALLBACK : status;
+        if (bt.status) bt.status[r] = (bt.fallback == 1 && status == PSR_CONVERGED) ? PSR_REFINE_FALLBACK : status;
         if (bt.iters) bt.iters[r] = counter + (fb ? bt.iters[r] : 0);
         if (bt.ts_steps) bt.ts_steps[r] = ts + (fb ? bt.ts_steps[r] : 0);
         if (bt.fnorm) bt.fnorm[r] = fn;
@@ -1310,6 +1413,8 @@ __device__ void solve_one(Ctx &cx, const WS<TJ> &w, const Batch &bt, int64_t r) 
 constexpr int kMaxSolveWarps = 4;   // the solver kernel's block holds at most 4 warps (128 threads)
 constexpr int kDefaultSolveWarps = 2;   // measured best at K = 53 for both forms (finer shared-memory packing)
 template <class TJ, bool SOOT, bool FDJ = false>
+// queue[0]: work-queue tickets; queue[1]: warps that found the queue empty (both zeroed
+// by the launcher).
 __global__ void __launch_bounds__(128, PSR_MIN_BLOCKS) solve_kernel(DevMech M, Batch bt, Opts o, int *queue,
                                                                    size_t ws_per_warp) {
     extern __shared__ __align__(16) char smem[];
@@ -1322,12 +1427,23 @@ __global__ void __launch_bounds__(128, PSR_MIN_BLOCKS) solve_kernel(DevMech M, B
     cx.mult = bt.rate_mult;
     cx.K = M.K;
     cx.n = M.K + 1 + ns;
+    cx.idle = queue + 1;
     const int64_t nwork = bt.list ? int64_t(*bt.list_len) : bt.B;
+    // warps that never get a reactor go idle at once: the threshold counts working warps only
+    cx.handoff_at = 0;
+    if (o.handoff_pct > 0) {
+        const int64_t W = int64_t(gridDim.x) * (blockDim.x >> 5);
+        const int64_t working = W < nwork ? W : nwork;
+        cx.handoff_at = int((W - working) + (working * o.handoff_pct + 99) / 100);
+    }
     while (true) {
         int p = 0;
         if (lane == 0) p = atomicAdd(queue, 1);
         p = __shfl_sync(kFull, p, 0);
-        if (p >= nwork) break;
+        if (p >= nwork) {
+            if (lane == 0) atomicAdd(queue + 1, 1);
+            break;
+        }
         const int64_t r = bt.list ? int64_t(bt.list[p]) : int64_t(p);
         solve_one<TJ, SOOT, FDJ>(cx, w, bt, r);
     }

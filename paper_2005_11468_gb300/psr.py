@@ -23,6 +23,7 @@ CONVERGED_STATES = (PSR_CONVERGED, PSR_REFINE_FALLBACK)
 PSR_FP64, PSR_MIXED = 0, 1
 PSR_ADIABATIC, PSR_FIXED_T = 0, 1
 PSR_PATH_AUTO, PSR_PATH_WARP, PSR_PATH_BLOCK = 0, 1, 2
+PSR_LU_CUDA_CORES, PSR_LU_TF32, PSR_LU_3XTF32 = 0, 1, 3
 
 
 class PsrError(RuntimeError):
@@ -50,7 +51,7 @@ class COptions(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_int32), ("mixed_fallback", ctypes.c_int32),
                 ("jacobian", ctypes.c_int32), ("mixed_max_newton", ctypes.c_int32),
                 ("jac_age", ctypes.c_int32), ("ts_linear", ctypes.c_int32), ("path", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("handoff", ctypes.c_int32), ("lu_tensor", ctypes.c_int32)]
 
 
 _lib = None
@@ -90,6 +91,7 @@ def lib():
         L.psr_batch_solve_multi.argtypes = [ctypes.POINTER(vp), i32, i64, dp, dp] + [dp] * 8 + [dp] * 5 + \
             [ctypes.POINTER(COptions), vp]
         L.psr_pipe_probe.argtypes = [i32, i64, i32, i32, dp, vp]
+        L.psr_batch_lu_solve_tc.argtypes = [i64, i32, dp, dp, dp, dp, i32, vp]
         _lib = L
     return _lib
 
@@ -128,6 +130,8 @@ class Options:
     jac_age: int = 1
     ts_linear: int = 150
     path: int = 0
+    handoff: int = -1
+    lu_tensor: int = 0
 
     def to_c(self):
         o = COptions()
@@ -311,13 +315,26 @@ def eval_jacobian_fd(mech: Mechanism, Y_in, T_in, tau, P, Y, T, rate_mult=None, 
 
 
 def batch_lu_solve(A, r, precision=PSR_FP64):
-    """Solve A_b x_b = r_b for a batch of n x n systems (n <= 64) by the solver's LU."""
+    """Solve A_b x_b = r_b for a batch of n x n systems (n <= 512) by the solver's LU."""
     import torch
     B, n, _ = A.shape
     x = torch.empty((B, n), dtype=torch.float64, device=A.device)
     ok = torch.empty(B, dtype=torch.int32, device=A.device)
     _check(lib().psr_batch_lu_solve(B, n, _ptr(A, torch.float64, (B, n, n), "A"), _ptr(r, torch.float64, (B, n), "r"),
                                     x.data_ptr(), ok.data_ptr(), precision, _stream()))
+    return x, ok
+
+
+def batch_lu_solve_tc(A, r, lu_tensor=PSR_LU_TF32):
+    """psr_batch_lu_solve_tc: the FP32 LU with the trailing update on the tensor cores
+    (TF32 or 3xTF32) for n >= 96 (smaller n: CUDA cores)."""
+    import torch
+    B, n, _ = A.shape
+    x = torch.empty((B, n), dtype=torch.float64, device=A.device)
+    ok = torch.empty(B, dtype=torch.int32, device=A.device)
+    _check(lib().psr_batch_lu_solve_tc(B, n, _ptr(A, torch.float64, (B, n, n), "A"),
+                                       _ptr(r, torch.float64, (B, n), "r"), x.data_ptr(), ok.data_ptr(), lu_tensor,
+                                       _stream()))
     return x, ok
 
 
@@ -449,9 +466,11 @@ def eval_rates(mech: Mechanism, Y, T, P, rate_mult=None, out=None):
 
 
 PROBE_FMA64, PROBE_FMA32, PROBE_EXP64, PROBE_LOG64, PROBE_DIV64 = 0, 1, 2, 3, 4
+PROBE_SATOM32, PROBE_SATOM32_SAME, PROBE_SATOM64, PROBE_SATOM64_SAME = 5, 6, 7, 8
 # operations per thread and iteration of each probe (psr_probe.h): flops for the FMA
-# probes, calls for exp / log / division
-PROBE_OPS = {PROBE_FMA64: 16, PROBE_FMA32: 32, PROBE_EXP64: 8, PROBE_LOG64: 8, PROBE_DIV64: 8}
+# probes, calls for exp / log / division, atomics for the shared-memory atomic probes
+PROBE_OPS = {PROBE_FMA64: 16, PROBE_FMA32: 32, PROBE_EXP64: 8, PROBE_LOG64: 8, PROBE_DIV64: 8,
+             PROBE_SATOM32: 8, PROBE_SATOM32_SAME: 8, PROBE_SATOM64: 8, PROBE_SATOM64_SAME: 8}
 
 
 def pipe_probe(kind, iters, blocks, threads, sink):

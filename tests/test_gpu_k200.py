@@ -100,6 +100,15 @@ def test_block_lu_parity(env, n):
 
 
 _REF = {}
+_POOL = {}
+
+
+def _oracle_pool(idx):
+    key = tuple(idx)
+    if key not in _POOL:
+        from tests import oracle_pool
+        _POOL[key] = oracle_pool.solve([(NAME, b) for b in idx])
+    return _POOL[key]
 
 
 def _oracle(env, idx):
@@ -112,7 +121,8 @@ def _oracle(env, idx):
 @pytest.mark.parametrize("precision", [psr.PSR_FP64, psr.PSR_MIXED])
 def test_k200_full_size_solve(env, precision):
     """The 2048-reactor launch the benchmark times: every converged reactor has
-    ||F|| <= 1e-8 and conserves elements to 1e-12; two sampled reactors match the oracle."""
+    ||F|| <= 1e-8 and conserves elements to 1e-12; eight sampled reactors (oracle in a
+    process pool) match the oracle, at least six on the same branch."""
     mech, batch = env["mech"], env["batch"]
     t = _t(env, batch)
     out = psr.batch_solve(env["gm"], t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"],
@@ -124,19 +134,23 @@ def test_k200_full_size_solve(env, precision):
     Y, T = out["Y"].cpu().numpy(), out["T"].cpu().numpy()
     elem = ((Y[conv] - batch.Y_in[conv]) / mech.W) @ mech.comp
     assert np.max(np.abs(elem)) <= 1e-12
-    idx = [0, 1]
-    ref = _oracle(env, idx)
-    for j, b in enumerate(idx):
-        if ref["status"][j] != O.CONVERGED:
+    idx = [0, 1, 97, 500, 1024, 1500, 1999, 2047]
+    res = _oracle_pool(idx)
+    compared = 0
+    for b in idx:
+        x, status, _, _ = res[(NAME, b)]
+        if status != O.CONVERGED:
             continue
         assert st[b] in psr.CONVERGED_STATES
-        if abs(T[b] - ref["T"][j]) > 1.0:
+        if abs(T[b] - x[-1]) > 1.0:
             Fo = O.gas_residual(mech, np.r_[Y[b], T[b]][None], O.inlet_of(batch, b))[0]
             assert np.max(np.abs(Fo)) <= 1e-7
             continue
-        big = ref["Y"][j] > Y_MIN
-        assert np.max(np.abs(Y[b][big] - ref["Y"][j][big]) / ref["Y"][j][big]) <= Y_REL
-        assert abs(T[b] - ref["T"][j]) <= T_ABS
+        big = x[:-1] > Y_MIN
+        assert np.max(np.abs(Y[b][big] - x[:-1][big]) / x[:-1][big]) <= Y_REL
+        assert abs(T[b] - x[-1]) <= T_ABS
+        compared += 1
+    assert compared >= 6, f"only {compared} of {len(idx)} sampled K = 200 reactors compared"
 
 
 def test_k200_adjoint(env):

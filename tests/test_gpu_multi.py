@@ -123,7 +123,9 @@ def test_graph_capture_replays_the_call(env):
     import torch
     mb = synth.mixed_batch(env["specs"], B=384)
     t = _dev(env, mb)
-    opts = psr.Options(precision=psr.PSR_MIXED)
+    # without the handoff of stragglers, which depends on timing, so that warp-path rows
+    # are bit-reproducible
+    opts = psr.Options(precision=psr.PSR_MIXED, handoff=0)
     eager = _multi(env, t, opts)
     torch.cuda.synchronize()
     out = {k: torch.empty_like(v) for k, v in eager.items()}

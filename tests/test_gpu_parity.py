@@ -274,9 +274,10 @@ def test_rate_multipliers(dev):
     sub = batch.subset(idx)
     t = to_dev(sub, dev)
     gm = gpu_mech("k10_b64")
-    a = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"])
+    det = psr.Options(handoff=0)          # bit-reproducible: no timing-dependent handoff
+    a = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"], opts=det)
     ones = torch.ones(mech.I, dtype=torch.float64, device=dev)
-    b = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"], rate_mult=ones)
+    b = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"], rate_mult=ones, opts=det)
     assert torch.equal(a["Y"], b["Y"]) and torch.equal(a["T"], b["T"])
     lnm = np.random.Generator(np.random.PCG64(3)).uniform(-0.5, 0.5, mech.I)
     c = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"],
@@ -298,8 +299,9 @@ def test_host_entry_matches_device(dev):
     sub = batch.subset(range(16))
     t = to_dev(sub, dev)
     gm = gpu_mech("k10_b64")
-    a = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"])
-    h = psr.batch_solve_host(gm, sub.Y_in, sub.T_in, sub.tau, sub.P, sub.Y0, sub.T0)
+    det = psr.Options(handoff=0)          # bit-reproducible: no timing-dependent handoff
+    a = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"], opts=det)
+    h = psr.batch_solve_host(gm, sub.Y_in, sub.T_in, sub.tau, sub.P, sub.Y0, sub.T0, opts=det)
     np.testing.assert_array_equal(h["Y"], a["Y"].cpu().numpy())
     np.testing.assert_array_equal(h["status"], a["status"].cpu().numpy())
 
@@ -312,12 +314,14 @@ def test_edge_cases(dev):
     e = to_dev(batch.subset([]), dev)
     out = psr.batch_solve(gm, e["Y_in"], e["T_in"], e["tau"], e["P"], e["Y0"], e["T0"])
     assert out["Y"].shape == (0, mech.K)
-    # ragged sizes give the same per-reactor answers as the full batch
+    # ragged sizes give the same per-reactor answers as the full batch (without the
+    # timing-dependent handoff of stragglers, the warp path is bit-reproducible)
+    det = psr.Options(handoff=0)
     full = to_dev(batch, dev)
-    ref = psr.batch_solve(gm, full["Y_in"], full["T_in"], full["tau"], full["P"], full["Y0"], full["T0"])
+    ref = psr.batch_solve(gm, full["Y_in"], full["T_in"], full["tau"], full["P"], full["Y0"], full["T0"], opts=det)
     for B in (1, 3, 33):
         s = to_dev(batch.subset(range(B)), dev)
-        o = psr.batch_solve(gm, s["Y_in"], s["T_in"], s["tau"], s["P"], s["Y0"], s["T0"])
+        o = psr.batch_solve(gm, s["Y_in"], s["T_in"], s["tau"], s["P"], s["Y0"], s["T0"], opts=det)
         assert torch.equal(o["Y"], ref["Y"][:B]) and torch.equal(o["status"], ref["status"][:B])
     # tau -> 0: outlet = inlet
     s = to_dev(batch.subset(range(8)), dev)
@@ -348,7 +352,7 @@ def test_autotune_picks_a_shape_with_identical_results(dev):
     sub = batch.subset(range(1024))
     t = to_dev(sub, dev)
     gm = gpu_mech("k53_b4096")
-    base = psr.Options(precision=psr.PSR_MIXED)
+    base = psr.Options(precision=psr.PSR_MIXED, handoff=0)
     tuned = psr.autotune(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"], base)
     shapes = {(psr.PSR_PATH_WARP, w, b) for w, b in ((1, 0), (2, 0), (3, 0), (4, 0), (2, 2), (2, 3), (2, 4))}
     shapes.add((psr.PSR_PATH_BLOCK, 0, 0))
