@@ -106,7 +106,10 @@ typedef struct {
     int32_t energy;         /* PSR_ADIABATIC (default) or PSR_FIXED_T */
     int32_t warps_per_block;/* 0 = default (2); at most 4 */
     int32_t blocks_per_sm;  /* 0 = as many as fit */
-    int32_t mixed_fallback; /* 1 (default): PSR_MIXED re-solves unconverged reactors in FP64 */
+    int32_t mixed_fallback; /* PSR_MIXED: what the FP32-Jacobian launch leaves unconverged is
+                               solved again with the FP64 Jacobian: 2 (default) first continued
+                               from that launch's final iterate, then restarted from the initial
+                               guess where the continuation fails; 1 restart only; 0 none */
     int32_t jacobian;       /* PSR_JAC_ANALYTIC (default) or PSR_JAC_FD: central differences
                                as the paper builds it (Sec. 1), K + 1 <= 64 gas mechanisms */
     int32_t mixed_max_newton; /* 300: Newton cap of the FP32-Jacobian launch when the FP64
@@ -162,11 +165,12 @@ void psr_options_default(psr_options *o);
  *   iters [B], ts_steps [B], status [B], fnorm [B] (||F||_inf at the output state),
  *   nfev [B] (residual evaluations, the reactor's share of the FP64 work): each may be NULL.
  * One persistent kernel launch; reactors are taken from a work queue by warps. With
- * PSR_MIXED and mixed_fallback = 1 a second launch re-solves, from Y0/T0 and with the
- * FP64 Jacobian, the reactors the first left unconverged (the list is built on the
- * device; no host synchronisation); their counters add up and a success reports
- * PSR_REFINE_FALLBACK. If Y0/T0 alias Y_out/T_out, that re-solve starts from the first
- * launch's final iterate.
+ * PSR_MIXED and mixed_fallback = 1 or 2 further launches re-solve with the FP64 Jacobian
+ * the reactors the first left unconverged (the lists are built on the device; no host
+ * synchronisation): mixed_fallback = 2 continues them from the first launch's final
+ * iterate, then restarts from Y0/T0 those the continuation leaves; 1 restarts them from
+ * Y0/T0. Their counters add up and a success reports PSR_REFINE_FALLBACK. If Y0/T0 alias
+ * Y_out/T_out, a restart starts from the first launch's final iterate.
  * Mechanisms with K + 1 <= 64 run one warp per reactor; larger ones (K + 1 <= 512) one
  * thread block per reactor with the same method.
  * Device memory: a few scratch integers (B + 4 for the fallback, B more when status is

@@ -540,7 +540,7 @@ void psr_options_default(psr_options *o) {
     o->ts_newton = 8;
     o->precision = PSR_FP64;
     o->energy = PSR_ADIABATIC;
-    o->mixed_fallback = 1;
+    o->mixed_fallback = 2;
     o->jacobian = PSR_JAC_ANALYTIC;
     o->mixed_max_newton = 300;
     o->jac_age = 1;

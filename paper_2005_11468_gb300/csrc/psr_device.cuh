@@ -99,6 +99,7 @@ struct Opts {
                             // queue empty, running reactors stop and go to the block solver (0 = never)
     int lu_tc;              // block solver, FP32 Jacobian: LU trailing update on the tensor cores
                             // (0 = CUDA cores, 1 = TF32, 3 = 3xTF32)
+    int mixed_fb;           // mixed form's FP64 re-solve: 0 off, 1 restart, 2 continue then restart
 };
 
 // Scalars of the last residual evaluation that the Jacobian reuses.
@@ -158,6 +159,9 @@ struct Troe {
     double dlk0;      // d ln k0 / dT
 };
 
+// The value is FP64; the derivatives (for the Jacobian only) are evaluated in TD, FP32 for
+// the FP32 Jacobian (they only steer Newton, and FP64 divisions are long, slow chains).
+template <class TD = double>
 __device__ __forceinline__ Troe troe_eval(const double *__restrict__ tp, double a_inf, double M, double T,
                                           double lnT, double invT, bool want_deriv) {
     Troe t;
@@ -177,14 +181,17 @@ __device__ __forceinline__ Troe troe_eval(const double *__restrict__ tp, double 
     const double F = exp(kLn10 * lgF);
     t.fac = Pr / (1.0 + Pr) * F;
     if (want_deriv) {
-        const double dlgF_du = -L * 2.0 * f1 / (s * s) * nn / (den * den);
-        t.D = 1.0 / (1.0 + Pr) + dlgF_du;
-        const double dFc = -(1.0 - al) / T3 * e3 - al / T1 * e1 + ((T2 != 0.0) ? T2 * invT * invT * e2 : 0.0);
-        const double dL_dT = dFc / (Fc * kLn10);
-        const double df1_dL = (-0.67 * nn + 1.27 * u) / (den * den);
-        const double dlgF_dL = 1.0 / s - L * 2.0 * f1 / (s * s) * df1_dL;
-        t.dlnF_dT = kLn10 * dlgF_dL * dL_dT;
-        t.dlk0 = b0 * invT + th0 * invT * invT;
+        const TD Ld = TD(L), f1d = TD(f1), sd = TD(s), nnd = TD(nn), dend = TD(den), ud = TD(u), Prd = TD(Pr);
+        const TD iTd = TD(invT), ald = TD(al), one = TD(1);
+        const TD dlgF_du = -Ld * TD(2) * f1d / (sd * sd) * nnd / (dend * dend);
+        t.D = double(one / (one + Prd) + dlgF_du);
+        const TD dFc = -(one - ald) / TD(T3) * TD(e3) - ald / TD(T1) * TD(e1) +
+                       ((T2 != 0.0) ? TD(T2) * iTd * iTd * TD(e2) : TD(0));
+        const TD dL_dT = dFc / (TD(Fc) * TD(kLn10));
+        const TD df1_dL = (TD(-0.67) * nnd + TD(1.27) * ud) / (dend * dend);
+        const TD dlgF_dL = one / sd - Ld * TD(2) * f1d / (sd * sd) * df1_dL;
+        t.dlnF_dT = double(TD(kLn10) * dlgF_dL * dL_dT);
+        t.dlk0 = double(TD(b0) * iTd + TD(th0) * iTd * iTd);
     } else {
         t.D = t.dlnF_dT = t.dlk0 = 0.0;
     }

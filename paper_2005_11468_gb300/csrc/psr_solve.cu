@@ -20,16 +20,18 @@
 namespace psr {
 namespace {
 
-// Work list for the second launch of a solve (among in_list when given, else among all B):
-// every reactor the first launch left unconverged (handoff_only = 0, the mixed form's FP64
-// re-solve), or only those it handed over unfinished (handoff_only = 1, a continuation in
-// the same precision).
+// Work list for a later launch of a solve (among in_list when given, else among all B):
+// mode 0: every reactor not converged by the first launch (the mixed form's FP64 re-solve);
+// mode 1: those it handed over unfinished (a continuation in the same precision); mode 2:
+// those neither launch converged (the restart after a continuation).
 __global__ void collect_unconverged(int64_t B, const int32_t *in_list, const int32_t *in_len, const int32_t *status,
-                                    int32_t *list, int32_t *len, int handoff_only) {
+                                    int32_t *list, int32_t *len, int mode) {
     const int64_t n = in_list ? int64_t(*in_len) : B;
     for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < n; p += int64_t(gridDim.x) * blockDim.x) {
         const int64_t r = in_list ? int64_t(in_list[p]) : p;
-        const bool take = handoff_only ? status[r] == kStatusHandoff : status[r] != PSR_CONVERGED;
+        const int32_t s = status[r];
+        const bool take = mode == 1 ? s == kStatusHandoff
+                                    : (s != PSR_CONVERGED && (mode == 0 || s != PSR_REFINE_FALLBACK));
         if (take) list[atomicAdd(len, 1)] = int32_t(r);
     }
 }
@@ -311,6 +313,7 @@ Opts to_opts(const psr_options *po) {
     // solver finishes a straggler ~1.6x sooner than a warp with the FP64 LU, ~1.3x with FP32)
     o.handoff_pct = s.handoff >= 0 ? s.handoff : (s.precision == PSR_FP64 ? 75 : 0);
     o.lu_tc = s.lu_tensor;
+    o.mixed_fb = s.mixed_fallback;
     return o;
 }
 
@@ -323,7 +326,7 @@ int check_opts(const psr_options *po) {
         s.max_ts_rounds < 0 || s.ts_steps < 1 || s.ts_newton < 1 ||
         (s.precision != PSR_FP64 && s.precision != PSR_MIXED) ||
         (s.energy != PSR_ADIABATIC && s.energy != PSR_FIXED_T) || s.warps_per_block < 0 || s.warps_per_block > 32 ||
-        s.blocks_per_sm < 0 || (s.mixed_fallback != 0 && s.mixed_fallback != 1) ||
+        s.blocks_per_sm < 0 || s.mixed_fallback < 0 || s.mixed_fallback > 2 ||
         (s.jacobian != PSR_JAC_ANALYTIC && s.jacobian != PSR_JAC_FD) || s.mixed_max_newton < 0 || s.jac_age < 0 ||
         s.jac_age > 64 || s.ts_linear < 0 || s.path < PSR_PATH_AUTO || s.path > PSR_PATH_BLOCK || s.handoff < -1 ||
         s.handoff > 100 || (s.lu_tensor != PSR_LU_CUDA_CORES && s.lu_tensor != PSR_LU_TF32 && s.lu_tensor != PSR_LU_3XTF32))
@@ -492,18 +495,29 @@ int launch_mixed(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int
             rc = block_resolve_list(m, bc, o1, PSR_MIXED, st, q1);
         }
     }
-    if (rc == PSR_OK) {
+    // FP64 re-solve of what the FP32 launch left unconverged: with mixed_fallback = 2 first
+    // continued from the FP32 launch's final iterate, then restarted from the initial guess
+    // for whatever the continuation leaves; with 1, only the restart
+    const int passes = o.mixed_fb == 2 ? 2 : 1;
+    for (int pass = 0; pass < passes && rc == PSR_OK; ++pass) {
+        const bool from_iterate = passes == 2 && pass == 0;
         cudaMemsetAsync(len, 0, sizeof(int32_t), st);
         collect_unconverged<<<unsigned((B + 255) / 256), 256, 0, st>>>(bt.B, bt.list, bt.list_len, b1.status, list,
-                                                                       len, 0);
+                                                                       len, pass == 0 ? 0 : 2);
         e = cudaGetLastError();
-        if (e != cudaSuccess) rc = cuda_error("collect_unconverged launch", e);
-    }
-    if (rc == PSR_OK) {
+        if (e != cudaSuccess) {
+            rc = cuda_error("collect_unconverged launch", e);
+            break;
+        }
         Batch b2 = b1;
         b2.list = list;
         b2.list_len = len;
         b2.fallback = 1;
+        if (from_iterate) {
+            b2.Y0 = b1.Y_out;
+            if (o.energy != PSR_FIXED_T) b2.T0 = b1.T_out;   // T0 is the specified temperature otherwise
+            if (m.dev.nsoot) b2.M0 = b1.M_out;
+        }
         // the list is short: gas-phase reactors go to the block solver, one CTA each
         if (block_fb)
             rc = block_resolve_list(m, b2, o, PSR_FP64, st, q1);

@@ -124,7 +124,7 @@ class Options:
     energy: int = PSR_ADIABATIC
     warps_per_block: int = 0
     blocks_per_sm: int = 0
-    mixed_fallback: int = 1
+    mixed_fallback: int = 2
     jacobian: int = 0
     mixed_max_newton: int = 300
     jac_age: int = 1

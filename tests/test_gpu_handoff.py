@@ -73,7 +73,7 @@ def test_handoff_call_replays_from_a_cuda_graph(dev):
     captured in a CUDA graph and replayed: the eager call's converged set and roots."""
     import torch
     _, mech, batch = workload("k53_b4096")
-    t = to_dev(batch.subset(range(1024)), dev)
+    t = to_dev(batch, dev)            # the handoff needs at least two reactors per warp
     gm = gpu_mech("k53_b4096")
     opts = psr.Options(precision=psr.PSR_FP64, handoff=1)
     eager = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"], opts=opts)
@@ -93,6 +93,6 @@ def test_handoff_call_replays_from_a_cuda_graph(dev):
     torch.cuda.synchronize()
     cs = torch.tensor(psr.CONVERGED_STATES, device=dev, dtype=torch.int32)
     ok_e, ok_g = torch.isin(eager["status"], cs), torch.isin(out["status"], cs)
-    assert ok_g.float().mean().item() >= 0.99 and (ok_e != ok_g).sum().item() <= 3
+    assert ok_g.float().mean().item() >= 0.99 and (ok_e != ok_g).sum().item() <= 8
     both = ok_e & ok_g & ((out["T"] - eager["T"]).abs() < 1.0)
     torch.testing.assert_close(out["T"][both], eager["T"][both], rtol=0, atol=T_ABS)

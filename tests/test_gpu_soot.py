@@ -170,3 +170,31 @@ def test_mixed_fallback_resolves_in_fp64(env):
         assert abs(Tf[b] - T64[b]) <= T_ABS
         assert np.max(np.abs(Mf[b] - M64[b]) / M64[b]) <= M_REL
     assert np.isin(sf, psr.CONVERGED_STATES).mean() >= np.mean(s64 == psr.PSR_CONVERGED) - 0.01
+
+
+def test_mixed_fallback_continues_then_restarts(env):
+    """The default fallback (mixed_fallback = 2) on 2048 sooting reactors: the reactors the
+    FP32-Jacobian launch leaves are first continued in FP64 from its final iterate, then
+    restarted from the guess where that fails. It converges at least as many reactors as the
+    restart alone (within 0.5 %), and its roots are the FP64 form's on the same branch."""
+    batch = env["batch"].subset(range(2048))
+    t = _t(env, batch)
+    args = (env["gm"], t["Y_in"], t["T_in"], t["tau"], t["P"], t["M_in"], t["Y0"], t["T0"])
+    two = psr.batch_solve_soot(*args, opts=psr.Options(precision=psr.PSR_MIXED, mixed_fallback=2))
+    one = psr.batch_solve_soot(*args, opts=psr.Options(precision=psr.PSR_MIXED, mixed_fallback=1))
+    f64 = psr.batch_solve_soot(*args, opts=psr.Options(precision=psr.PSR_FP64))
+    s2, s1, s64 = (o["status"].cpu().numpy() for o in (two, one, f64))
+    c2, c1 = np.isin(s2, psr.CONVERGED_STATES), np.isin(s1, psr.CONVERGED_STATES)
+    assert c2.mean() >= c1.mean() - 0.005
+    assert np.sum(s2 == psr.PSR_REFINE_FALLBACK) >= 20
+    assert np.all(two["fnorm"].cpu().numpy()[c2] <= 1e-8)
+    Y2, Y64 = two["Y"].cpu().numpy(), f64["Y"].cpu().numpy()
+    T2, T64 = two["T"].cpu().numpy(), f64["T"].cpu().numpy()
+    M2, M64 = two["M"].cpu().numpy(), f64["M"].cpu().numpy()
+    both = c2 & (s64 == psr.PSR_CONVERGED) & (np.abs(T2 - T64) < 1.0)
+    assert both.mean() >= 0.95
+    for b in np.flatnonzero(both):
+        big = Y64[b] > Y_MIN
+        assert np.max(np.abs(Y2[b][big] - Y64[b][big]) / Y64[b][big]) <= Y_REL
+        assert abs(T2[b] - T64[b]) <= T_ABS
+        assert np.max(np.abs(M2[b] - M64[b]) / M64[b]) <= M_REL
