@@ -695,9 +695,10 @@ def e2e_soot(ctx, r, steps):
 
 
 def launches_per_step(r):
-    """Our kernels per timed mixed step: the FP32-Jacobian solve, and with unconverged
-    reactors the list kernel and the FP64 re-solve (both always enqueued)."""
-    return 3
+    """Our kernels per timed mixed step: the FP32-Jacobian solve, then for the FP64 re-solve
+    of what it leaves the list kernel and the continuation from its iterate, and the list
+    kernel and the restart from the guess (all always enqueued, lists built on the device)."""
+    return 5
 
 
 def run_ours(args):

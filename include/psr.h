@@ -112,9 +112,10 @@ typedef struct {
                                guess where the continuation fails; 1 restart only; 0 none */
     int32_t jacobian;       /* PSR_JAC_ANALYTIC (default) or PSR_JAC_FD: central differences
                                as the paper builds it (Sec. 1), K + 1 <= 64 gas mechanisms */
-    int32_t mixed_max_newton; /* 300: Newton cap of the FP32-Jacobian launch when the FP64
-                               re-solve follows (0 = max_newton); reactors it leaves are
-                               re-solved in FP64 with max_newton */
+    int32_t mixed_max_newton; /* -1 (default: 300 for gas mechanisms, 200 with soot moments):
+                               Newton cap of the FP32-Jacobian launch when the FP64 re-solve
+                               follows (0 = max_newton); reactors it leaves are re-solved in
+                               FP64 with max_newton per pass */
     int32_t jac_age;        /* 1 (default): a fresh Jacobian and LU every Newton iteration;
                                A > 1: the factors serve up to A iterations while undamped steps
                                keep shrinking (any failure retries with fresh factors) */

@@ -542,7 +542,7 @@ void psr_options_default(psr_options *o) {
     o->energy = PSR_ADIABATIC;
     o->mixed_fallback = 2;
     o->jacobian = PSR_JAC_ANALYTIC;
-    o->mixed_max_newton = 300;
+    o->mixed_max_newton = -1;
     o->jac_age = 1;
     o->ts_linear = 150;
     o->handoff = -1;

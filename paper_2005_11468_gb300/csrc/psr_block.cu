@@ -419,18 +419,14 @@ __device__ void b_eval_F(const DevMech &M, const BWS<TJ> &w, const double *y, do
 // concentration-Jacobian blocks (shared-memory atomics), a dense third-body part per
 // column, Euler sums and T-derivatives per species, the transform to (Y, T) and the
 // energy row of Eq. (3). Same chain and precision as the warp solver's Jacobian.
+// The per-reaction pass of the block Jacobian in FP64 (also the FP32 Jacobian's fallback
+// for K + 1 > 256): see the warp solver's jac_reactions for the quantities.
 template <class TJ>
-__device__ void b_eval_J(const DevMech &M, const BWS<TJ> &w, const double *c, const Mix &mx, double tau,
-                         int energy, const double *__restrict__ mult) {
-    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const int K = M.K, I = M.I, n = K + 1, P = w.P;
-    __syncthreads();
-    const double wd = (t < K) ? w.v[t] : 0.0;
-    __syncthreads();
-    for (size_t idx = t; idx < size_t(n) * P; idx += kBT) w.J[idx] = TJ(0);
-    if (t < K) w.v[t] = 0.0;
-    __syncthreads();
-    const double T = mx.T, invT = mx.invT;
+__device__ void b_jac_reactions_f64(const DevMech &M, const BWS<TJ> &w, const Mix &mx,
+                                    const double *__restrict__ mult) {
+    const int t = threadIdx.x;
+    const int K = M.K, I = M.I, P = w.P;
+    const double invT = mx.invT;
     for (int i = t; i < I; i += kBT) {
         const int16_t *sl6 = M.slots + size_t(i) * 6;
         int s[6];
@@ -504,6 +500,122 @@ __device__ void b_eval_J(const DevMech &M, const BWS<TJ> &w, const double *c, co
         w.q[i] = g;       // per-reaction Euler sum
         w.kf[i] = dqdT;   // and T-derivative replace q and kf
     }
+}
+
+// The same pass with FP32 arithmetic for the FP32 Jacobian (the pieces only steer Newton;
+// FP64 instructions are the scarce resource): FP32 copies of the concentrations in the
+// reduction scratch (free during the pass, K + 1 <= 256), the dense third-body part
+// accumulated in FP32 in rhs (free until the energy row), ln K_c's T-derivative from the
+// FP64 H/RT. g_i and d q_i / dT are stored in FP64 for the species sums.
+template <class TJ>
+__device__ void b_jac_reactions_f32(const DevMech &M, const BWS<TJ> &w, const Mix &mx,
+                                    const double *__restrict__ mult) {
+    const int t = threadIdx.x;
+    const int K = M.K, I = M.I, P = w.P;
+    float *Cf = reinterpret_cast<float *>(w.red);
+    float *vf = reinterpret_cast<float *>(w.rhs);
+    if (t <= K) Cf[t] = float(w.C[t]);
+    if (t < K) vf[t] = 0.0f;
+    __syncthreads();
+    const double invT = mx.invT;
+    const float invTf = float(invT), Ctot = float(mx.Ctot);
+    for (int i = t; i < I; i += kBT) {
+        const int16_t *sl6 = M.slots + size_t(i) * 6;
+        int s[6];
+        float cs[6];
+#pragma unroll
+        for (int u = 0; u < 6; ++u) {
+            s[u] = __ldg(sl6 + u);
+            cs[u] = Cf[s[u]];
+        }
+        const float Pf = cs[0] * cs[1] * cs[2], Pr_ = cs[3] * cs[4] * cs[5];
+        const float d0 = cs[1] * cs[2], d1 = cs[0] * cs[2], d2 = cs[0] * cs[1];
+        const float d3 = cs[4] * cs[5], d4 = cs[3] * cs[5], d5 = cs[3] * cs[4];
+        const float kf = float(w.kf[i]), kr = float(w.kr[i]);
+        const float m = mult ? float(__ldg(mult + __ldg(M.orig + i))) : 1.0f;
+        const int typ = __ldg(M.type + i);
+        float Mc = 1.0f;
+        if (typ != kElem) {
+            Mc = Ctot;
+            for (int e = __ldg(M.eff_ptr + i); e < __ldg(M.eff_ptr + i + 1); ++e)
+                Mc += __ldg(M.eff_val_f + e) * Cf[__ldg(M.eff_sp + e)];
+        }
+        const float sM = (typ == kThirdBody) ? Mc : 1.0f;
+        const float dlkf = __ldg(M.beta_f + i) * invTf + __ldg(M.theta_f + i) * invTf * invTf;
+        const float dlKc = float(((w.hRT[s[3]] + w.hRT[s[4]] + w.hRT[s[5]]) - (w.hRT[s[0]] + w.hRT[s[1]] + w.hRT[s[2]]) -
+                                  __ldg(M.dnu_d + i)) * invT);
+        float dlkfe = dlkf, dqdM = 0.0f;
+        if (typ == kThirdBody) {
+            dqdM = m * (kf * Pf - kr * Pr_);
+        } else if (typ == kTroe) {
+            const int tr = __ldg(M.troe_row + i);
+            dlkfe = dlkf + float(w.tX[tr]);
+            dqdM = m * (kf * Pf - kr * Pr_) * float(w.tD[tr]) / Mc;
+        }
+        const float dlkre = dlkfe - dlKc;
+        const float Af = m * sM * kf, Ar = m * sM * kr;
+        const int nf = (s[0] < K) + (s[1] < K) + (s[2] < K), nr = (s[3] < K) + (s[4] < K) + (s[5] < K);
+        float g = Af * float(nf) * Pf - Ar * float(nr) * Pr_;
+        if (typ != kElem) g += dqdM * Mc;
+        const float dqdT = Af * Pf * dlkfe - Ar * Pr_ * dlkre;
+        const int16_t *pp = M.part + size_t(i) * 6;
+        const int8_t *pn = M.part_nu + size_t(i) * 6;
+        const int8_t *pfm = M.part_fm + size_t(i) * 6;
+        const int8_t *prm = M.part_rm + size_t(i) * 6;
+        int pl[6];
+        TJ pnu[6], val[6];
+#pragma unroll
+        for (int u = 0; u < 6; ++u) {
+            pl[u] = __ldg(pp + u);
+            pnu[u] = TJ(__ldg(pn + u));
+            const int fm = __ldg(pfm + u), rm = __ldg(prm + u);
+            const float dfl = slot_deriv_f(fm, d0, d1, d2);
+            const float drl = slot_deriv_f(rm, d3, d4, d5);
+            val[u] = TJ(Af * dfl - Ar * drl);
+        }
+        const TJ dqdM_t = TJ(dqdM);
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+            if (pl[r] >= K || pnu[r] == TJ(0)) continue;
+            TJ *row = w.J + size_t(pl[r]) * P;
+#pragma unroll
+            for (int u = 0; u < 6; ++u) {
+                if (pl[u] >= K) continue;
+                atomicAdd(row + pl[u], pnu[r] * val[u]);
+            }
+            if (typ != kElem) {
+                atomicAdd(vf + pl[r], float(pnu[r]) * dqdM);
+                for (int e = __ldg(M.eff_ptr + i); e < __ldg(M.eff_ptr + i + 1); ++e)
+                    atomicAdd(row + __ldg(M.eff_sp + e), pnu[r] * dqdM_t * eff_v<TJ>(M, e));
+            }
+        }
+        w.q[i] = double(g);
+        w.kf[i] = double(dqdT);
+    }
+}
+
+
+template <class TJ>
+__device__ void b_eval_J(const DevMech &M, const BWS<TJ> &w, const double *c, const Mix &mx, double tau,
+                         int energy, const double *__restrict__ mult) {
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int K = M.K, I = M.I, n = K + 1, P = w.P;
+    __syncthreads();
+    const double wd = (t < K) ? w.v[t] : 0.0;
+    __syncthreads();
+    for (size_t idx = t; idx < size_t(n) * P; idx += kBT) w.J[idx] = TJ(0);
+    if (t < K) w.v[t] = 0.0;
+    __syncthreads();
+    const double T = mx.T, invT = mx.invT;
+    if constexpr (sizeof(TJ) == 4) {
+        if (K + 1 <= kRedSlots * kBW * 2) {
+            b_jac_reactions_f32(M, w, mx, mult);
+        } else {
+            b_jac_reactions_f64(M, w, mx, mult);
+        }
+    } else {
+        b_jac_reactions_f64(M, w, mx, mult);
+    }
     __syncthreads();
     double sk = 0.0, wT = 0.0, vk = 0.0;
     if (t < K) {
@@ -513,7 +625,11 @@ __device__ void b_eval_J(const DevMech &M, const BWS<TJ> &w, const double *c, co
             sk += nu * w.q[r];
             wT += nu * w.kf[r];
         }
-        vk = w.v[t];
+        if constexpr (sizeof(TJ) == 4) {
+            vk = (K + 1 <= kRedSlots * kBW * 2) ? double(reinterpret_cast<const float *>(w.rhs)[t]) : w.v[t];
+        } else {
+            vk = w.v[t];
+        }
     }
     const double rho = mx.rho, Wbar = mx.Wbar, RT = kRu * T;
     double eJ = 0.0;
@@ -570,6 +686,7 @@ __device__ void b_eval_J(const DevMech &M, const BWS<TJ> &w, const double *c, co
     if (t < n) w.J[size_t(t) * P + t] = TJ(double(w.J[size_t(t) * P + t]) + c[t]);
     __syncthreads();
 }
+
 
 // ---------------------------------------------------------------- LU (partial pivoting)
 // Candidate for the next pivot: largest |a| by integer key, ties to the lower row (a NaN
@@ -1456,7 +1573,8 @@ int block_solve(const Mech &m, const Batch &bt, const Opts &o, int precision, bo
         Batch b1 = bt;
         if (!bt.status) b1.status = scr + 4 + B;
         Opts first = o;   // the FP32 launch stops at the mixed_max_newton cap (see the warp solver)
-        if (o.mixed_max_newton > 0 && o.mixed_max_newton < o.max_newton) first.max_newton = o.mixed_max_newton;
+        const int cap = o.mixed_max_newton >= 0 ? o.mixed_max_newton : 300;   // the gas default
+        if (cap > 0 && cap < o.max_newton) first.max_newton = cap;
         rc = launch_block<float>(m, b1, first, bps_req, st, scr);
         if (rc == PSR_OK) {
             cudaMemsetAsync(len, 0, sizeof(int32_t), st);

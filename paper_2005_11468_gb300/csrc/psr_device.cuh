@@ -136,6 +136,14 @@ __device__ __forceinline__ double slot_deriv(int m, double d0, double d1, double
     return v;
 }
 
+__device__ __forceinline__ float slot_deriv_f(int m, float d0, float d1, float d2) {
+    const float first = (m & 1) ? d0 : ((m & 2) ? d1 : ((m & 4) ? d2 : 0.0f));
+    const int rest = m & (m - 1);
+    float v = first + ((rest & 2) ? d1 : ((rest & 4) ? d2 : 0.0f));
+    if (m == 7) v += d2;
+    return v;
+}
+
 // ---------------------------------------------------------------- thermo (NASA-7)
 __device__ __forceinline__ void nasa7(const double *__restrict__ nasa, int k, double T, double lnT, double invT,
                                       double &cpR, double &hRT, double &sR, double &dcpR) {

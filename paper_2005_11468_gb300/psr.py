@@ -126,7 +126,7 @@ class Options:
     blocks_per_sm: int = 0
     mixed_fallback: int = 2
     jacobian: int = 0
-    mixed_max_newton: int = 300
+    mixed_max_newton: int = -1
     jac_age: int = 1
     ts_linear: int = 150
     path: int = 0

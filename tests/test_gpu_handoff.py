@@ -39,7 +39,10 @@ def test_handoff_reaches_the_same_roots(dev, precision):
     bar of each other, every converged reactor at ||F|| <= 1e-8, no Newton budget overrun,
     and the eager handoff visibly moves reactors to the block solver."""
     ref = _solve(dev, precision, 0)
-    cap = psr.Options().max_newton + (psr.Options().mixed_max_newton if precision == psr.PSR_MIXED else 0)
+    # the reactor's budget: max_newton, or in the mixed form the FP32 launch's gas cap (300)
+    # plus an FP64 continuation and an FP64 restart of max_newton each
+    cap = psr.Options().max_newton * (2 if precision == psr.PSR_MIXED else 1) + \
+        (300 if precision == psr.PSR_MIXED else 0)
     for h in (50, 1):
         got = _solve(dev, precision, h)
         c0, c1 = np.isin(ref["status"], psr.CONVERGED_STATES), np.isin(got["status"], psr.CONVERGED_STATES)

@@ -145,7 +145,7 @@ def test_mixed_fallback_resolves_in_fp64(env):
     args = (env["gm"], t["Y_in"], t["T_in"], t["tau"], t["P"], t["M_in"], t["Y0"], t["T0"])
     # the fallback's first launch stops at mixed_max_newton; the same cap without fallback
     # is that launch on its own
-    cap = psr.Options().mixed_max_newton
+    cap = 200                                  # the FP32 launch's default cap with soot moments
     one = psr.batch_solve_soot(*args, opts=psr.Options(precision=psr.PSR_MIXED, mixed_fallback=0, max_newton=cap))
     fb = psr.batch_solve_soot(*args, opts=psr.Options(precision=psr.PSR_MIXED, mixed_fallback=1))
     f64 = psr.batch_solve_soot(*args, opts=psr.Options(precision=psr.PSR_FP64))
