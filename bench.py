@@ -50,9 +50,10 @@ EXTRA = ("k10_b64", "k53soot_b16384", "k200_b2048", MIXED)
 METRIC = "converged PSR solves/s, mixed vs FP64 form on one GB300 at ‖F‖∞≤1e-8; roofline %"
 RATES_METRIC = "rate evaluations/s (kf, kr, q, wdot per state; Eqs. (4)-(9)) at T = 1800 K"
 UNIT = "solves/s"
-# dram__bytes_read + write of one mixed-form launch of solve_kernel<float> on k53_b4096,
-# from an ncu capture of the current build; None until the kernel is captured again
-K53_TRAFFIC_BYTES = None
+# dram__bytes_read.sum + dram__bytes_write.sum of one mixed-form launch of
+# solve_kernel<float> on k53_b4096, from an ncu capture of the current build; set to None
+# whenever that kernel changes, until it is captured again
+K53_TRAFFIC_BYTES = 5133824 + 5990656
 
 
 def parse():
@@ -123,49 +124,57 @@ def mech_counts(spec):
 
 def work_counts(spec, nfev, iters, precision):
     """Algorithmic work of the solves, summed over reactors, in the categories of the
-    scope's measurement section: FP64 flops, FP32 flops (the mixed form's Jacobian and
-    LU), and exp, log and division calls counted as calls. An FMA is two flops.
+    scope's measurement section: FP64 flops, FP32 flops, and exp, log and division calls
+    counted as calls (an FMA is two flops; an FP32 division is counted as 8 FP32 flops).
+    Each piece is counted in the precision the solver computes it in: the residual, its
+    exponentials and the species sums in FP64; the Jacobian's per-reaction pieces, the Troe
+    derivatives, the scatter, transform, LU and substitutions in the Jacobian's precision
+    (FP32 in the mixed form).
 
     Per residual evaluation (nfev per reactor): per species NASA-7 c_p, H, S and dc_p
-    (37 flops), concentration and the energy sums (16), wdot gather (2 per entry),
-    residual (4); per reaction ln k (4), ln K_c (8), slot products (4), q (3), two exp;
-    per third-body efficiency 2 flops; per Troe row 4-5 exp (P_r, F_cent terms, F), two
-    log10, 8 divisions and ~65 flops (value and derivatives); per evaluation 2 log and
-    4 divisions. With soot: one MOMIC source evaluation (39 exp, 29 log, ~600 flops) and
-    six moment balances (6 exp, ~40 flops).
-    Per Newton iteration (iters per reactor): analytic Jacobian, per reaction ~85 FP64
-    flops of derivative pieces and 2 flops per Jacobian entry it adds (in the Jacobian's
-    precision), 3 per efficiency entry and participant; species sums 4 per gather entry;
-    transform 4 K^2 and energy-row column sums 2 K^2 (Jacobian precision); the LU
-    2 n^3 / 3 (Jacobian precision). With soot, the soot block adds 17 source evaluations
-    and 9 n chained entries (12 flops each). Per residual one pair of triangular solves,
-    2 n^2 flops and n divisions (Jacobian precision)."""
+    (37 flops), concentration and the energy sums (16), residual (4); wdot gather 2 per
+    entry; per reaction ln k (4), ln K_c (8), slot products (4), q (3) and two exp; per
+    third-body efficiency 2 flops; per Troe row 4-5 exp (P_r, F_cent terms, F), two log10,
+    2 divisions and ~30 flops for the value, 6 divisions and ~35 flops for the derivatives;
+    per evaluation 2 log and 4 divisions. With soot: one MOMIC source evaluation (39 exp,
+    29 log, ~600 flops) and six moment balances (6 exp, ~40 flops).
+    Per Newton iteration (iters per reactor): per reaction ~85 flops of derivative pieces
+    and 2 flops per Jacobian entry it adds, 3 per efficiency entry and participant; species
+    sums 4 per gather entry and ~15 per species (FP64); transform 4 K^2 and energy-row column
+    sums 2 K^2; the LU 2 n^3 / 3. With soot, the soot block adds 17 source evaluations and
+    9 n chained entries (12 flops each, FP64). Per residual one pair of triangular solves,
+    2 n^2 flops and n divisions."""
     K, I, n_tb, n_troe, n_t2, n_eff, nnz, pairs = mech_counts(spec)
     soot = spec.soot is not None
     n = K + 1 + (6 if soot else 0)
     nf, it = float(np.sum(nfev)), float(np.sum(iters))
-    # per residual evaluation
-    f64_F = K * (37 + 16 + 4) + 2 * nnz + I * 19 + 2 * n_eff + n_tb + n_troe * 65
+    mixed = precision == "mixed"
+    # per residual evaluation: FP64 parts, and the Troe derivatives in the Jacobian's precision
+    f64_F = K * (37 + 16 + 4) + 2 * nnz + I * 19 + 2 * n_eff + n_tb + n_troe * 30
     exp_F = 2 * I + 4 * n_troe + n_t2
     log_F = 2 + 2 * n_troe
-    div_F = 4 + 8 * n_troe
+    div_F = 4 + 2 * n_troe
+    jac_F, jdiv_F = n_troe * 35, n_troe * 6
     if soot:
         f64_F += 600 + 40
         exp_F += 39 + 6
         log_F += 29
     # per Newton iteration
-    f64_J = I * 85 + 4 * nnz + 15 * K
-    j_J = 2 * pairs + 3 * n_eff * 3 + 4 * K * K + 2 * K * K + 2.0 * n ** 3 / 3.0
+    f64_J = 4 * nnz + 15 * K
+    jac_J = I * 85 + 2 * pairs + 3 * n_eff * 3 + 4 * K * K + 2 * K * K + 2.0 * n ** 3 / 3.0
     exp_J = log_J = 0.0
     if soot:
         f64_J += 17 * 600 + 9 * n * 12
         exp_J += 17 * 39
         log_J += 17 * 29
-    j_S = 2.0 * n * n
+    jac_S, jdiv_S = 2.0 * n * n, n
     c = {"fp64_flop": nf * f64_F + it * f64_J, "fp32_flop": 0.0, "exp": nf * exp_F + it * exp_J,
-         "log": nf * log_F + it * log_J, "div": nf * (div_F + n)}
-    jp = "fp32_flop" if precision == "mixed" else "fp64_flop"
-    c[jp] += it * j_J + nf * j_S
+         "log": nf * log_F + it * log_J, "div": nf * div_F}
+    if mixed:
+        c["fp32_flop"] += nf * (jac_F + 8 * jdiv_F + jac_S + 8 * jdiv_S) + it * jac_J
+    else:
+        c["fp64_flop"] += nf * (jac_F + jac_S) + it * jac_J
+        c["div"] += nf * (jdiv_F + jdiv_S)
     return c
 
 

@@ -142,6 +142,9 @@ typedef struct {
                                (tcgen05, TF32 operands, FP32 accumulation in tensor memory);
                                3XTF32 splits each operand into two TF32 parts (three products)
                                for FP32-like accuracy. Other solves ignore it. */
+    int32_t block_threads;  /* threads per reactor on the block solver: 0 (default) or 512, or
+                               256 for mechanisms with K + 1 <= 256 (more resident blocks
+                               when the Jacobian sits in global memory, cheaper barriers) */
 } psr_options;
 
 /* LU trailing update (psr_options.lu_tensor) */
@@ -273,13 +276,15 @@ int psr_eval_jacobian_fd(const psr_mech *m, int64_t B,
  * library): solves the caller's sample batch (device arrays as psr_batch_solve, B >= 1,
  * ideally a few thousand reactors like the production batches) once per candidate shape
  * and writes the one with the most converged solves per second into opt->path,
- * opt->warps_per_block and opt->blocks_per_sm; every other field of *opt is used as
- * given. Candidates for K + 1 <= 64: one warp per reactor with 1..4 warps per block and
- * 2-warp blocks capped at 2..4 blocks per SM, and one 512-thread block per reactor;
- * larger mechanisms have the block path only. Synchronises cuda_stream; allocates and
- * frees output scratch on it. The roots do not depend on the shape: within a path the
- * arithmetic is the same, and the two paths reach the same roots within the solver's
- * tolerance (the block path's Jacobian sums its contributions in another order).
+ * opt->warps_per_block, opt->blocks_per_sm and opt->block_threads; every other field of
+ * *opt is used as given. Candidates: threads per reactor (one warp for K + 1 <= 64, or a
+ * thread block of 512 or, for K + 1 <= 256, 256 threads for gas mechanisms); on the warp
+ * path 1..4 warps per block and 2-warp blocks capped at 2..4 blocks per SM; on the block
+ * path (larger mechanisms) 0 (as many as fit), 1 or 2 blocks per SM. Synchronises
+ * cuda_stream; allocates and frees output scratch on it. The roots do not depend on the
+ * shape: within a path the arithmetic is the same, and the paths reach the same roots
+ * within the solver's tolerance (the block path's Jacobian sums its contributions in
+ * another order).
  * Errors: PSR_E_ARG (NULL, soot mechanism, B outside 1..2^24), PSR_E_CUDA, PSR_E_OOM. */
 int psr_autotune(const psr_mech *m, int64_t B,
                  const double *Y_in, const double *T_in, const double *tau, const double *P,

@@ -14,7 +14,7 @@ SOURCES = ["psr_solve.cu", "psr_block.cu", "mech.cpp", "pipe_probe.cu"]
 # psr_solve_inst.cu is built once per solve_kernel instantiation (Jacobian precision,
 # soot, finite-difference Jacobian): six objects that compile in parallel.
 INSTANCES = [(tj, soot, fdj) for soot, fdj in ((0, 0), (0, 1), (1, 0)) for tj in ("float", "double")]
-HEADERS = ["psr_internal.h", "psr_device.cuh", "psr_warp.cuh"]
+HEADERS = ["psr_internal.h", "psr_device.cuh", "psr_warp.cuh", "psr_tc.cuh"]
 
 
 def _nvcc():
@@ -47,10 +47,11 @@ def build(force=False):
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     units = [(s, [], "") for s in SOURCES]
+    units.append(("psr_block.cu", ["-DPSR_BLOCK_THREADS=256"], ".bt256"))   # the 256-thread block solver
     units += [("psr_solve_inst.cu", [f"-DPSR_INST_TJ={tj}", f"-DPSR_INST_SOOT={soot}", f"-DPSR_INST_FDJ={fdj}"],
                f".{tj}{soot}{fdj}") for tj, soot, fdj in INSTANCES]
     # the slowest units first, so that they start before the small ones take the cores
-    units.sort(key=lambda u: 0 if u[0] == "psr_solve_inst.cu" else 1)
+    units.sort(key=lambda u: 0 if u[0] in ("psr_solve_inst.cu", "psr_block.cu") else 1)
     with concurrent.futures.ThreadPoolExecutor(min(len(units), max(2, os.cpu_count() or 2))) as ex:
         objs = list(ex.map(lambda u: _compile(u, nvcc), units))
     tmp = LIB + ".tmp"

@@ -16,10 +16,26 @@
 #include "psr_internal.h"
 #include "psr_tc.cuh"
 
+// Built twice: with 512 threads per block (every entry point) and with 256 (the solver,
+// for mechanisms with K + 1 <= 256: more resident blocks per SM when the Jacobian lives in
+// global memory, cheaper block barriers); each build's entry points sit in its own
+// namespace, psr::bt512 or psr::bt256.
+#ifndef PSR_BLOCK_THREADS
+#define PSR_BLOCK_THREADS 512
+#endif
+#if PSR_BLOCK_THREADS == 512
+#define PSR_BLOCK_NS bt512
+#elif PSR_BLOCK_THREADS == 256
+#define PSR_BLOCK_NS bt256
+#else
+#error "PSR_BLOCK_THREADS must be 256 or 512"
+#endif
+
 namespace psr {
+namespace PSR_BLOCK_NS {
 namespace {
 
-constexpr int kBT = 512;          // threads per block
+constexpr int kBT = PSR_BLOCK_THREADS;   // threads per block
 constexpr int kBW = kBT / 32;     // warps per block
 constexpr int kMaxBlockN = kBT;   // unknowns per reactor: thread j owns component j
 constexpr int kRedSlots = 8;      // values reduced together
@@ -630,6 +646,7 @@ __device__ void b_eval_J(const DevMech &M, const BWS<TJ> &w, const double *c, co
         } else {
             vk = w.v[t];
         }
+        w.v[t] = vk;   // the row transform below reads it per row (warps over rows)
     }
     const double rho = mx.rho, Wbar = mx.Wbar, RT = kRu * T;
     double eJ = 0.0;
@@ -1332,7 +1349,7 @@ __device__ void b_solve_one(BCtx &cx, const BWS<TJ> &w, const Batch &bt, int64_t
 
 // ---------------------------------------------------------------- kernels
 template <class TJ>
-__global__ void __launch_bounds__(kBT, 1) block_solve_kernel(DevMech M, Batch bt, Opts o, int *queue, TJ *Jglob) {
+__global__ void __launch_bounds__(kBT, 512 / kBT) block_solve_kernel(DevMech M, Batch bt, Opts o, int *queue, TJ *Jglob) {
     extern __shared__ __align__(128) char smem[];
     const int K = M.K, n = K + 1;
     const size_t slot = size_t(n) * pitch_of(n);
@@ -1370,7 +1387,7 @@ __global__ void block_collect_unconverged(int64_t B, const int32_t *in_list, con
 
 // residual or Jacobian at given states, one block per state (grid-stride over states)
 template <class TJ>
-__global__ void __launch_bounds__(kBT, 1) block_eval_kernel(DevMech M, Batch bt, int energy, int want_J,
+__global__ void __launch_bounds__(kBT, 512 / kBT) block_eval_kernel(DevMech M, Batch bt, int energy, int want_J,
                                                             double *out, RatesOut ro, TJ *Jglob) {
     extern __shared__ __align__(128) char smem[];
     const int K = M.K, n = K + 1;
@@ -1411,7 +1428,7 @@ __global__ void __launch_bounds__(kBT, 1) block_eval_kernel(DevMech M, Batch bt,
 // Adjoint sensitivities at given (converged) states (the warp solver's formula):
 // J^T lam = g with the FP64 factors, then
 // dL/d ln m_i = (tau q_i / rho) [sum_k lam_k W_k nu_ki - lam_T dH_i / (c_p T)].
-__global__ void __launch_bounds__(kBT, 1) block_adjoint_kernel(DevMech M, Batch bt, int energy, const double *g,
+__global__ void __launch_bounds__(kBT, 512 / kBT) block_adjoint_kernel(DevMech M, Batch bt, int energy, const double *g,
                                                                double *grad, double *lam_out, int32_t *ok,
                                                                double *Jglob) {
     extern __shared__ __align__(128) char smem[];
@@ -1463,7 +1480,7 @@ __global__ void __launch_bounds__(kBT, 1) block_adjoint_kernel(DevMech M, Batch 
 }
 
 template <class TJ>
-__global__ void __launch_bounds__(kBT, 1) block_lu_kernel(int64_t B, int n, const double *A, const double *rhs,
+__global__ void __launch_bounds__(kBT, 512 / kBT) block_lu_kernel(int64_t B, int n, const double *A, const double *rhs,
                                                           double *x, int32_t *ok, TJ *Jglob, int tc) {
     extern __shared__ __align__(128) char smem[];
     const size_t slot = size_t(n) * pitch_of(n);
@@ -1550,7 +1567,8 @@ int block_resolve_list(const Mech &m, const Batch &bt, const Opts &o, int precis
 
 int block_check(const Mech &m) {
     if (m.dev.nsoot) return set_error(PSR_E_UNSUPPORTED, "soot moments need K + 7 <= 64 (warp solver)");
-    if (m.K + 1 > kMaxBlockN) return set_error(PSR_E_UNSUPPORTED, "the block solver handles at most 512 unknowns");
+    if (m.K + 1 > kMaxBlockN)
+        return set_error(PSR_E_UNSUPPORTED, "the block solver handles at most " + std::to_string(kMaxBlockN) + " unknowns");
     return PSR_OK;
 }
 
@@ -1669,4 +1687,5 @@ int block_lu(int64_t B, int n, const double *A, const double *r, double *x, int3
                                   : block_lu_t<double>(B, n, A, r, x, ok, st);
 }
 
+}  // namespace PSR_BLOCK_NS
 }  // namespace psr

@@ -100,6 +100,7 @@ struct Opts {
     int lu_tc;              // block solver, FP32 Jacobian: LU trailing update on the tensor cores
                             // (0 = CUDA cores, 1 = TF32, 3 = 3xTF32)
     int mixed_fb;           // mixed form's FP64 re-solve: 0 off, 1 restart, 2 continue then restart
+    int block_threads;      // block solver threads per reactor: 0 (= 512), 256 or 512
 };
 
 // Scalars of the last residual evaluation that the Jacobian reuses.
@@ -206,17 +207,53 @@ __device__ __forceinline__ Troe troe_eval(const double *__restrict__ tp, double 
     return t;
 }
 
-// Host launchers of the block-per-reactor solver (psr_block.cu), for mechanisms whose
-// K + 1 unknowns exceed one warp's 64.
-int block_check(const Mech &m);
-int block_resolve_list(const Mech &m, const Batch &bt, const Opts &o, int precision, cudaStream_t st, int *queue);
-int block_solve(const Mech &m, const Batch &bt, const Opts &o, int precision, bool fallback, int bps_req,
-                cudaStream_t st);
-int block_eval(const Mech &m, const Batch &bt, int energy, int want_J, int precision, double *out, cudaStream_t st,
-               RatesOut ro = RatesOut{});
-int block_adjoint(const Mech &m, const Batch &bt, int energy, const double *g, double *grad, double *lam_out,
-                  int32_t *ok, cudaStream_t st);
-int block_lu(int64_t B, int n, const double *A, const double *r, double *x, int32_t *ok, int precision,
-             cudaStream_t st, int lu_tc = 0);
+// Host launchers of the block-per-reactor solver (psr_block.cu, built with 512 and with
+// 256 threads per block), for mechanisms whose K + 1 unknowns exceed one warp's 64.
+#define PSR_BLOCK_DECLS                                                                                           \
+    int block_check(const Mech &m);                                                                               \
+    int block_resolve_list(const Mech &m, const Batch &bt, const Opts &o, int precision, cudaStream_t st,         \
+                           int *queue);                                                                           \
+    int block_solve(const Mech &m, const Batch &bt, const Opts &o, int precision, bool fallback, int bps_req,     \
+                    cudaStream_t st);                                                                             \
+    int block_eval(const Mech &m, const Batch &bt, int energy, int want_J, int precision, double *out,            \
+                   cudaStream_t st, RatesOut ro = RatesOut{});                                                    \
+    int block_adjoint(const Mech &m, const Batch &bt, int energy, const double *g, double *grad, double *lam_out, \
+                      int32_t *ok, cudaStream_t st);                                                              \
+    int block_lu(int64_t B, int n, const double *A, const double *r, double *x, int32_t *ok, int precision,     \
+                 cudaStream_t st, int lu_tc = 0);
+namespace bt512 {
+PSR_BLOCK_DECLS
+}
+namespace bt256 {
+PSR_BLOCK_DECLS
+}
+#undef PSR_BLOCK_DECLS
+
+// Threads per reactor of the block solver: o.block_threads (0 = 512), 256 only where the
+// K + 1 unknowns fit.
+inline bool block256(const Mech &m, const Opts &o) { return o.block_threads == 256 && m.K + 1 <= 256; }
+inline int block_check(const Mech &m) { return bt512::block_check(m); }
+inline int block_resolve_list(const Mech &m, const Batch &bt, const Opts &o, int precision, cudaStream_t st,
+                              int *queue) {
+    return block256(m, o) ? bt256::block_resolve_list(m, bt, o, precision, st, queue)
+                          : bt512::block_resolve_list(m, bt, o, precision, st, queue);
+}
+inline int block_solve(const Mech &m, const Batch &bt, const Opts &o, int precision, bool fallback, int bps_req,
+                       cudaStream_t st) {
+    return block256(m, o) ? bt256::block_solve(m, bt, o, precision, fallback, bps_req, st)
+                          : bt512::block_solve(m, bt, o, precision, fallback, bps_req, st);
+}
+inline int block_eval(const Mech &m, const Batch &bt, int energy, int want_J, int precision, double *out,
+                      cudaStream_t st, RatesOut ro = RatesOut{}) {
+    return bt512::block_eval(m, bt, energy, want_J, precision, out, st, ro);
+}
+inline int block_adjoint(const Mech &m, const Batch &bt, int energy, const double *g, double *grad, double *lam_out,
+                         int32_t *ok, cudaStream_t st) {
+    return bt512::block_adjoint(m, bt, energy, g, grad, lam_out, ok, st);
+}
+inline int block_lu(int64_t B, int n, const double *A, const double *r, double *x, int32_t *ok, int precision,
+                    cudaStream_t st, int lu_tc = 0) {
+    return bt512::block_lu(B, n, A, r, x, ok, precision, st, lu_tc);
+}
 
 }  // namespace psr

@@ -314,6 +314,7 @@ Opts to_opts(const psr_options *po) {
     o.handoff_pct = s.handoff >= 0 ? s.handoff : (s.precision == PSR_FP64 ? 75 : 0);
     o.lu_tc = s.lu_tensor;
     o.mixed_fb = s.mixed_fallback;
+    o.block_threads = s.block_threads;
     return o;
 }
 
@@ -329,7 +330,8 @@ int check_opts(const psr_options *po) {
         s.blocks_per_sm < 0 || s.mixed_fallback < 0 || s.mixed_fallback > 2 ||
         (s.jacobian != PSR_JAC_ANALYTIC && s.jacobian != PSR_JAC_FD) || s.mixed_max_newton < -1 || s.jac_age < 0 ||
         s.jac_age > 64 || s.ts_linear < 0 || s.path < PSR_PATH_AUTO || s.path > PSR_PATH_BLOCK || s.handoff < -1 ||
-        s.handoff > 100 || (s.lu_tensor != PSR_LU_CUDA_CORES && s.lu_tensor != PSR_LU_TF32 && s.lu_tensor != PSR_LU_3XTF32))
+        s.handoff > 100 || (s.lu_tensor != PSR_LU_CUDA_CORES && s.lu_tensor != PSR_LU_TF32 && s.lu_tensor != PSR_LU_3XTF32) ||
+        (s.block_threads != 0 && s.block_threads != 256 && s.block_threads != 512))
         return set_error(PSR_E_ARG, "psr_options: value out of range");
     return PSR_OK;
 }
@@ -1030,18 +1032,26 @@ int psr_autotune(const psr_mech *m, int64_t B, const double *Y_in, const double 
     double *Yo = reinterpret_cast<double *>(buf), *To = Yo + nb * K, *fn = To + nb;
     int32_t *it = reinterpret_cast<int32_t *>(fn + nb), *ts = it + nb, *stt = ts + nb, *nf = stt + nb;
     // candidates: warps per block x block cap on the warp path; the block path has one shape
-    // candidates: threads per reactor (a warp, or a 512-thread block for gas mechanisms),
-    // and on the warp path warps per block x block cap
+    // candidates: threads per reactor (a warp, or a thread block of 512 or, where the
+    // K + 1 unknowns fit, 256 threads for gas mechanisms), on the warp path warps per block
+    // x block cap, on the block path a cap of 1-2 blocks per SM
     struct Cand {
-        int wpb, bps, path;
+        int wpb, bps, path, bt;
     };
     std::vector<Cand> cands;
+    const bool fits256 = m->m.K + 1 <= 256;
     if (warp_path(m)) {
-        for (int w : {1, 2, 3, 4}) cands.push_back({w, 0, PSR_PATH_WARP});
-        for (int b : {2, 3, 4}) cands.push_back({2, b, PSR_PATH_WARP});
-        if (!m->m.has_soot) cands.push_back({0, 0, PSR_PATH_BLOCK});
+        for (int w : {1, 2, 3, 4}) cands.push_back({w, 0, PSR_PATH_WARP, 0});
+        for (int b : {2, 3, 4}) cands.push_back({2, b, PSR_PATH_WARP, 0});
+        if (!m->m.has_soot) {
+            cands.push_back({0, 0, PSR_PATH_BLOCK, 512});
+            cands.push_back({0, 0, PSR_PATH_BLOCK, 256});
+        }
     } else {
-        cands.push_back({0, 0, PSR_PATH_BLOCK});
+        for (int bt : {512, 256}) {
+            if (bt == 256 && !fits256) continue;
+            for (int b : {0, 1, 2}) cands.push_back({0, b, PSR_PATH_BLOCK, bt});
+        }
     }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -1055,6 +1065,7 @@ int psr_autotune(const psr_mech *m, int64_t B, const double *Y_in, const double 
         trial.warps_per_block = cands[c].wpb;
         trial.blocks_per_sm = cands[c].bps;
         trial.path = cands[c].path;
+        trial.block_threads = cands[c].bt;
         cudaEventRecord(e0, st);
         rc = psr_batch_solve(m, B, Y_in, T_in, tau, P, Y0, T0, nullptr, Yo, To, it, ts, stt, fn, nf, &trial, st);
         cudaEventRecord(e1, st);
@@ -1086,6 +1097,7 @@ int psr_autotune(const psr_mech *m, int64_t B, const double *Y_in, const double 
         opt->warps_per_block = best.wpb;
         opt->blocks_per_sm = best.bps;
         opt->path = best.path;
+        opt->block_threads = best.bt;
     }
     return rc;
 }

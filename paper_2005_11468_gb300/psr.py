@@ -51,7 +51,8 @@ class COptions(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_int32), ("mixed_fallback", ctypes.c_int32),
                 ("jacobian", ctypes.c_int32), ("mixed_max_newton", ctypes.c_int32),
                 ("jac_age", ctypes.c_int32), ("ts_linear", ctypes.c_int32), ("path", ctypes.c_int32),
-                ("handoff", ctypes.c_int32), ("lu_tensor", ctypes.c_int32)]
+                ("handoff", ctypes.c_int32), ("lu_tensor", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32)]
 
 
 _lib = None
@@ -132,6 +133,7 @@ class Options:
     path: int = 0
     handoff: int = -1
     lu_tensor: int = 0
+    block_threads: int = 0
 
     def to_c(self):
         o = COptions()
@@ -444,7 +446,8 @@ def autotune(mech: Mechanism, Y_in, T_in, tau, P, Y0, T0, opts: Options = None) 
         mech.handle, B, _ptr(Y_in, f64, (B, K), "Y_in"), _ptr(T_in, f64, (B,), "T_in"), _ptr(tau, f64, (B,), "tau"),
         _ptr(P, f64, (B,), "P"), _ptr(Y0, f64, (B, K), "Y0"), _ptr(T0, f64, (B,), "T0"), ctypes.byref(o),
         _stream()))
-    return dataclasses.replace(base, warps_per_block=o.warps_per_block, blocks_per_sm=o.blocks_per_sm, path=o.path)
+    return dataclasses.replace(base, warps_per_block=o.warps_per_block, blocks_per_sm=o.blocks_per_sm, path=o.path,
+                               block_threads=o.block_threads)
 
 
 def eval_rates(mech: Mechanism, Y, T, P, rate_mult=None, out=None):

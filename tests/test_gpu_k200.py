@@ -213,3 +213,32 @@ def test_warp_block_boundary(env, K):
             big = r.x[:-1] > Y_MIN
             assert np.max(np.abs(Y[b][big] - r.x[:-1][big]) / r.x[:-1][big]) <= Y_REL
             assert abs(T[b] - r.x[-1]) <= T_ABS
+
+
+def test_k200_autotune_and_block_threads(env):
+    """psr_autotune on 608 reactors of the K = 200 batch picks one of its block-path shapes
+    (512 or 256 threads per reactor, 0-2 blocks per SM); the 256-thread solver on the same
+    reactors converges as the 512-thread one does and reaches the same roots within the bar,
+    in both forms."""
+    import torch
+    batch = env["batch"].subset(range(608))
+    t = _t(env, batch)
+    args = (env["gm"], t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"])
+    tuned = psr.autotune(*args, opts=psr.Options(precision=psr.PSR_MIXED))
+    assert (tuned.path, tuned.warps_per_block) == (psr.PSR_PATH_BLOCK, 0)
+    assert tuned.block_threads in (256, 512) and tuned.blocks_per_sm in (0, 1, 2)
+    for prec in (psr.PSR_FP64, psr.PSR_MIXED):
+        a = psr.batch_solve(*args, opts=psr.Options(precision=prec, block_threads=512))
+        b = psr.batch_solve(*args, opts=psr.Options(precision=prec, block_threads=256))
+        ca = np.isin(a["status"].cpu().numpy(), psr.CONVERGED_STATES)
+        cb = np.isin(b["status"].cpu().numpy(), psr.CONVERGED_STATES)
+        assert cb.mean() >= 0.99 and np.sum(ca != cb) <= 3
+        Ta, Tb = a["T"].cpu().numpy(), b["T"].cpu().numpy()
+        both = ca & cb & (np.abs(Ta - Tb) <= 1.0)
+        assert both.mean() >= 0.98
+        Ya, Yb = a["Y"].cpu().numpy()[both], b["Y"].cpu().numpy()[both]
+        big = Ya > Y_MIN
+        assert (np.abs(Yb - Ya)[big] / Ya[big]).max() <= Y_REL
+        assert np.abs(Ta[both] - Tb[both]).max() <= T_ABS
+    with pytest.raises(psr.PsrError):
+        psr.batch_solve(*args, opts=psr.Options(block_threads=300))

@@ -354,9 +354,9 @@ def test_autotune_picks_a_shape_with_identical_results(dev):
     gm = gpu_mech("k53_b4096")
     base = psr.Options(precision=psr.PSR_MIXED, handoff=0)
     tuned = psr.autotune(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"], base)
-    shapes = {(psr.PSR_PATH_WARP, w, b) for w, b in ((1, 0), (2, 0), (3, 0), (4, 0), (2, 2), (2, 3), (2, 4))}
-    shapes.add((psr.PSR_PATH_BLOCK, 0, 0))
-    assert (tuned.path, tuned.warps_per_block, tuned.blocks_per_sm) in shapes
+    shapes = {(psr.PSR_PATH_WARP, w, b, 0) for w, b in ((1, 0), (2, 0), (3, 0), (4, 0), (2, 2), (2, 3), (2, 4))}
+    shapes |= {(psr.PSR_PATH_BLOCK, 0, 0, 512), (psr.PSR_PATH_BLOCK, 0, 0, 256)}
+    assert (tuned.path, tuned.warps_per_block, tuned.blocks_per_sm, tuned.block_threads) in shapes
     assert tuned.precision == base.precision and tuned.ftol == base.ftol
     a = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"], opts=base)
     b = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"], opts=tuned)
