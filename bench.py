@@ -592,6 +592,16 @@ def measure_multi(ctx, steps, warmup, steps64, peaks, sampler=None, e2e=False):
     st64 = o64["status"].cpu().numpy()
     conv64 = int(np.isin(st64, psr.CONVERGED_STATES).sum())
     nfev64, iters64 = o64["nfev"].cpu().numpy(), o64["iters"].cpu().numpy()
+    # the same mixed-form call as one persistent launch over all mechanisms (persistent = 1)
+    pers_opts = psr.Options(precision=psr.PSR_MIXED, persistent=1)
+    o_pers = call(pers_opts)
+    ctx.barrier()
+    e0.record(ctx.stream)
+    call(pers_opts, o_pers)
+    e1.record(ctx.stream)
+    ctx.barrier()
+    ms_pers = e0.elapsed_time(e1)
+    conv_pers = int(np.isin(o_pers["status"].cpu().numpy(), psr.CONVERGED_STATES).sum())
     e_conv = e_t = 0.0
     h2d = d2h = 0
     if e2e:
@@ -611,8 +621,9 @@ def measure_multi(ctx, steps, warmup, steps64, peaks, sampler=None, e2e=False):
         h2d = sum(v.numel() * v.element_size() for v in host.values())
         d2h = sum(hout[k].numel() * hout[k].element_size() for k in ("Y", "T", "status"))
     total = sum(ms)
-    conv_all, conv64_all, e_conv = shard.reduce_sum(ctx.pg, [conv * steps, conv64, e_conv], ctx.dev)
-    total, ms64, e_t = shard.reduce_max(ctx.pg, [total, ms64, e_t], ctx.dev)
+    conv_all, conv64_all, e_conv, conv_pers = shard.reduce_sum(ctx.pg, [conv * steps, conv64, e_conv, conv_pers],
+                                                                 ctx.dev)
+    total, ms64, e_t, ms_pers = shard.reduce_max(ctx.pg, [total, ms64, e_t, ms_pers], ctx.dev)
     value = conv_all / (total / 1e3)
     value64 = conv64_all / (ms64 / 1e3)
 
@@ -632,8 +643,13 @@ def measure_multi(ctx, steps, warmup, steps64, peaks, sampler=None, e2e=False):
                          "residual_evals_mean": float(np.mean(nfev64)),
                          "roofline": class_roof(nfev64, iters64, "fp64", ms64 / 1e3)},
            "mixed_vs_fp64": value / value64 if value64 > 0 else None,
-           # per step: bucketing, and per class the solver, the unconverged list and the FP64 re-solve
-           "gpu_launches_per_step": 1 + 3 * len(specs)}
+           "persistent_launch": {"value": conv_pers / (ms_pers / 1e3), "unit": UNIT, "ms_per_step": ms_pers,
+                                 "steps": 1, "gpu_launches_per_step": 2,
+                                 "how": "persistent = 1: the bucketing kernel and one multi_solve_kernel over "
+                                        "all mechanisms, FP64 re-solves inside (direct call)"},
+           # per step: the bucketing kernel, then per mechanism the solver launch and the FP64
+           # re-solve passes (warp path: two list/re-solve pairs; block path: one)
+           "gpu_launches_per_step": 1 + sum(5 if sp.K + 1 <= 64 else 3 for sp in specs)}
     if e2e:
         res["e2e"] = {"value": e_conv / e_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
     for g in gms:

@@ -125,7 +125,7 @@ typedef struct {
                                clipped to [0.1, 8]); later steps, and all steps when 0, are
                                solved by damped Newton (<= ts_newton iterations, to ts_rtol) */
     int32_t path;           /* PSR_PATH_AUTO (default): one warp per reactor when K + 1 <= 64,
-                               else one 512-thread block; PSR_PATH_WARP / PSR_PATH_BLOCK force
+                               else one thread block (block_threads); PSR_PATH_WARP / PSR_PATH_BLOCK force
                                one (PSR_E_UNSUPPORTED where the mechanism does not fit it) */
     int32_t handoff;        /* -1 (default: 75 for PSR_FP64, 0 for PSR_MIXED) or 0..100. One warp
                                per reactor only: once this percentage of the launch's working
@@ -142,9 +142,25 @@ typedef struct {
                                (tcgen05, TF32 operands, FP32 accumulation in tensor memory);
                                3XTF32 splits each operand into two TF32 parts (three products)
                                for FP32-like accuracy. Other solves ignore it. */
-    int32_t block_threads;  /* threads per reactor on the block solver: 0 (default) or 512, or
-                               256 for mechanisms with K + 1 <= 256 (more resident blocks
-                               when the Jacobian sits in global memory, cheaper barriers) */
+    int32_t block_threads;  /* threads per reactor on the block solver: 512, or 256 for
+                               mechanisms with K + 1 <= 256 (more resident blocks when the
+                               Jacobian sits in global memory, cheaper barriers); 0 (default)
+                               = 256 where K + 1 <= 256, else 512 */
+    int32_t persistent;     /* psr_batch_solve_multi: 0 (default) = one launch sequence per
+                               mechanism on library streams forked from the caller's; 1 = one
+                               persistent launch over all mechanisms (256-thread blocks take
+                               block-solver reactors, largest K first, then their warps take
+                               warp-solver reactors; PSR_MIXED re-solves in FP64 in the same
+                               launch) where the batch allows it: analytic Jacobian, CUDA-core
+                               LU, K + 1 <= 256 for every mechanism on the block solver (and for
+                               all with PSR_MIXED and mixed_fallback > 0), else the per-mechanism
+                               layout. block_threads, warps_per_block, blocks_per_sm and handoff
+                               do not apply to the persistent launch. */
+    int32_t reserved0;      /* 0 */
+    int64_t spin_limit;     /* 0 (default: 2^25) or > 0: polls (about 1 us apart) a block of the
+                               persistent launch waits for first-pass reactors still running
+                               before it gives up on the FP64 re-solve it claimed (that reactor
+                               then keeps the FP32 pass's failure status) */
 } psr_options;
 
 /* LU trailing update (psr_options.lu_tensor) */
@@ -155,7 +171,7 @@ typedef struct {
 /* threads per reactor (psr_options.path) */
 #define PSR_PATH_AUTO 0
 #define PSR_PATH_WARP 1     /* one warp per reactor, K + 1 <= 64 (gas, or gas + soot with K + 7 <= 64) */
-#define PSR_PATH_BLOCK 2    /* one 512-thread block per reactor, gas mechanisms with K + 1 <= 512 */
+#define PSR_PATH_BLOCK 2    /* one thread block per reactor, gas mechanisms with K + 1 <= 512 */
 
 void psr_options_default(psr_options *o);
 

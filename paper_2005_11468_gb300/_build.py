@@ -14,7 +14,7 @@ SOURCES = ["psr_solve.cu", "psr_block.cu", "mech.cpp", "pipe_probe.cu"]
 # psr_solve_inst.cu is built once per solve_kernel instantiation (Jacobian precision,
 # soot, finite-difference Jacobian): six objects that compile in parallel.
 INSTANCES = [(tj, soot, fdj) for soot, fdj in ((0, 0), (0, 1), (1, 0)) for tj in ("float", "double")]
-HEADERS = ["psr_internal.h", "psr_device.cuh", "psr_warp.cuh", "psr_tc.cuh"]
+HEADERS = ["psr_internal.h", "psr_device.cuh", "psr_warp.cuh", "psr_block.cuh", "psr_tc.cuh"]
 
 
 def _nvcc():
@@ -38,7 +38,7 @@ def _compile(unit, nvcc):
 
 def build(force=False):
     """Compile every translation unit and link libpsr.so; returns the library path."""
-    srcs = ([os.path.join(CSRC, s) for s in SOURCES + ["psr_solve_inst.cu"] + HEADERS]
+    srcs = ([os.path.join(CSRC, s) for s in SOURCES + ["psr_solve_inst.cu", "psr_multi.cu"] + HEADERS]
             + [os.path.join(INCLUDE, h) for h in ("psr.h", "psr_probe.h")])
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
@@ -48,10 +48,13 @@ def build(force=False):
     nvcc = _nvcc()
     units = [(s, [], "") for s in SOURCES]
     units.append(("psr_block.cu", ["-DPSR_BLOCK_THREADS=256"], ".bt256"))   # the 256-thread block solver
+    # the persistent multi-mechanism kernel, once per first-pass Jacobian precision
+    units += [("psr_multi.cu", [f"-DPSR_MULTI_TJ={tj}", f"-DPSR_MULTI_ENTRY=multi_persistent_{tag}"], f".{tag}")
+              for tj, tag in (("float", "f32"), ("double", "f64"))]
     units += [("psr_solve_inst.cu", [f"-DPSR_INST_TJ={tj}", f"-DPSR_INST_SOOT={soot}", f"-DPSR_INST_FDJ={fdj}"],
                f".{tj}{soot}{fdj}") for tj, soot, fdj in INSTANCES]
     # the slowest units first, so that they start before the small ones take the cores
-    units.sort(key=lambda u: 0 if u[0] in ("psr_solve_inst.cu", "psr_block.cu") else 1)
+    units.sort(key=lambda u: 0 if u[0] in ("psr_multi.cu", "psr_solve_inst.cu", "psr_block.cu") else 1)
     with concurrent.futures.ThreadPoolExecutor(min(len(units), max(2, os.cpu_count() or 2))) as ex:
         objs = list(ex.map(lambda u: _compile(u, nvcc), units))
     tmp = LIB + ".tmp"

@@ -229,9 +229,34 @@ PSR_BLOCK_DECLS
 }
 #undef PSR_BLOCK_DECLS
 
-// Threads per reactor of the block solver: o.block_threads (0 = 512), 256 only where the
-// K + 1 unknowns fit.
-inline bool block256(const Mech &m, const Opts &o) { return o.block_threads == 256 && m.K + 1 <= 256; }
+// One persistent launch over the mechanism classes of psr_batch_solve_multi (psr_multi.cu):
+// ms[k] is the class in queue order k (classes [0, n_block) on the block solver, the rest on
+// the warp solver, each group by decreasing K), class_of[k] the index of its bucketed list
+// (lists + class_of[k] B, counts[class_of[k]] reactors). o1 = the first pass's options (the
+// FP32 pass's Newton cap for PSR_MIXED), o = the FP64 re-solve's. PSR_E_UNSUPPORTED
+// (nothing launched) where the batch needs what the persistent kernel leaves out.
+#define PSR_MULTI_DECL(name)                                                                                  \
+    int name(const Mech *const *ms, const int32_t *class_of, int n_cls, int n_block, const int32_t *counts,       \
+             const int32_t *lists, const Batch &bt, const Opts &o, const Opts &o1, int fb_passes,                \
+             long long spin_limit, cudaStream_t st);
+PSR_MULTI_DECL(multi_persistent_f32)
+PSR_MULTI_DECL(multi_persistent_f64)
+#undef PSR_MULTI_DECL
+inline int multi_persistent(const Mech *const *ms, const int32_t *class_of, int n_cls, int n_block,
+                            const int32_t *counts, const int32_t *lists, const Batch &bt, const Opts &o,
+                            const Opts &o1, int precision, int fb_passes, long long spin_limit, cudaStream_t st) {
+    return precision == PSR_MIXED
+               ? multi_persistent_f32(ms, class_of, n_cls, n_block, counts, lists, bt, o, o1, fb_passes, spin_limit, st)
+               : multi_persistent_f64(ms, class_of, n_cls, n_block, counts, lists, bt, o, o1, fb_passes, spin_limit, st);
+}
+
+// Threads per reactor of the block solver: o.block_threads, 256 only where the K + 1
+// unknowns fit; 0 = 256 where they fit, else 512 (at K = 200 the 256-thread solver is 7 %
+// faster with the FP32 Jacobian, one block per SM either way, and 23 % with the FP64
+// Jacobian in global memory, where two of its blocks fit on an SM).
+inline bool block256(const Mech &m, const Opts &o) {
+    return (o.block_threads == 256 || o.block_threads == 0) && m.K + 1 <= 256;
+}
 inline int block_check(const Mech &m) { return bt512::block_check(m); }
 inline int block_resolve_list(const Mech &m, const Batch &bt, const Opts &o, int precision, cudaStream_t st,
                               int *queue) {

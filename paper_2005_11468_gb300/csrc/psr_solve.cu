@@ -331,7 +331,8 @@ int check_opts(const psr_options *po) {
         (s.jacobian != PSR_JAC_ANALYTIC && s.jacobian != PSR_JAC_FD) || s.mixed_max_newton < -1 || s.jac_age < 0 ||
         s.jac_age > 64 || s.ts_linear < 0 || s.path < PSR_PATH_AUTO || s.path > PSR_PATH_BLOCK || s.handoff < -1 ||
         s.handoff > 100 || (s.lu_tensor != PSR_LU_CUDA_CORES && s.lu_tensor != PSR_LU_TF32 && s.lu_tensor != PSR_LU_3XTF32) ||
-        (s.block_threads != 0 && s.block_threads != 256 && s.block_threads != 512))
+        (s.block_threads != 0 && s.block_threads != 256 && s.block_threads != 512) || s.persistent < 0 ||
+        s.persistent > 1 || s.reserved0 != 0 || s.spin_limit < 0)
         return set_error(PSR_E_ARG, "psr_options: value out of range");
     return PSR_OK;
 }
@@ -983,6 +984,42 @@ int psr_batch_solve_multi(const psr_mech *const *mechs, int32_t n_mech, int64_t 
     if (e != cudaSuccess) {
         cudaFreeAsync(scr, st);
         return cuda_error("bucket_by_mechanism launch", e);
+    }
+    if (po.persistent && !o.jac_fd && !o.lu_tc) {
+        // one persistent launch: block-solver classes first, then warp-solver classes, each
+        // group by decreasing K
+        int order[kMaxMechs], n_block = 0;
+        const Mech *ms[kMaxMechs];
+        bool fits = true;
+        for (int c = 0; c < n_mech; ++c) order[c] = c;
+        auto on_block = [&](int c) { return po.path == PSR_PATH_BLOCK || !warp_path(mechs[c]); };
+        std::sort(order, order + n_mech, [&](int a, int b) {
+            if (on_block(a) != on_block(b)) return on_block(a);
+            return mechs[a]->m.K > mechs[b]->m.K;
+        });
+        const bool fb = po.precision == PSR_MIXED && po.mixed_fallback != 0;
+        for (int k = 0; k < n_mech; ++k) {
+            const Mech &mm = mechs[order[k]]->m;
+            ms[k] = &mm;
+            if (on_block(order[k])) ++n_block;
+            if ((on_block(order[k]) || fb) && mm.K + 1 > 256) fits = false;
+        }
+        if (po.path == PSR_PATH_WARP && n_block > 0) {
+            cudaFreeAsync(scr, st);
+            return set_error(PSR_E_UNSUPPORTED, "PSR_PATH_WARP: K + 1 <= 64 only");
+        }
+        if (fits) {
+            Batch bt{B, Y_in, T_in, tau, P, Y0, T0, nullptr, Y_out, T_out, fnorm, iters, ts_steps, stat, nfev};
+            bt.row_off = row_off;
+            Opts o1 = o;
+            if (po.precision == PSR_MIXED && fb) o1 = mixed_first(o, false);
+            o1.handoff_pct = 0;
+            const long long spin = po.spin_limit > 0 ? po.spin_limit : (1ll << 25);
+            rc = multi_persistent(ms, order, n_mech, n_block, counts, lists, bt, o, o1, po.precision,
+                                  fb ? (po.mixed_fallback == 2 ? 2 : 1) : 0, spin, st);
+            cudaFreeAsync(scr, st);
+            return rc;
+        }
     }
     // classes in order of decreasing size of the system, each on its own stream
     int order[kMaxMechs];

@@ -52,7 +52,8 @@ class COptions(ctypes.Structure):
                 ("jacobian", ctypes.c_int32), ("mixed_max_newton", ctypes.c_int32),
                 ("jac_age", ctypes.c_int32), ("ts_linear", ctypes.c_int32), ("path", ctypes.c_int32),
                 ("handoff", ctypes.c_int32), ("lu_tensor", ctypes.c_int32),
-                ("block_threads", ctypes.c_int32)]
+                ("block_threads", ctypes.c_int32), ("persistent", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("spin_limit", ctypes.c_int64)]
 
 
 _lib = None
@@ -134,6 +135,8 @@ class Options:
     handoff: int = -1
     lu_tensor: int = 0
     block_threads: int = 0
+    persistent: int = 0
+    spin_limit: int = 0
 
     def to_c(self):
         o = COptions()

@@ -1,7 +1,8 @@
 """The uneven batch (50/35/15 % of K = 10 / 53 / 200 reactors, 32768 in all, shuffled) in
-one call of psr_batch_solve_multi: against per-mechanism solves of the same reactors and,
-on sampled reactors, against the oracle; out-of-range mechanism ids; and a CUDA graph
-capture of the call replayed."""
+one call of psr_batch_solve_multi: the persistent launch against per-mechanism solves of
+the same reactors, against one launch sequence per mechanism and, on sampled reactors,
+against the oracle; the block path and the bounded wait inside the persistent launch;
+out-of-range mechanism ids; and a CUDA graph capture of the call replayed."""
 import numpy as np
 import pytest
 
@@ -49,14 +50,16 @@ def _rows(mb, Y, c, K):
         np.zeros((0, K))
 
 
-def test_uneven_batch_full_size(env):
-    """The 32768-reactor launch the benchmark times: each mechanism's reactors equal a
-    separate psr_batch_solve of that mechanism on the same reactors; sampled reactors of
-    every mechanism match the oracle."""
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_uneven_batch_full_size(env, persistent):
+    """The 32768-reactor call the benchmark times, in both layouts (one launch sequence per
+    mechanism, and the one persistent launch): each mechanism's reactors equal a separate
+    psr_batch_solve of that mechanism on the same reactors; sampled reactors of every
+    mechanism match the oracle."""
     import torch
     mb = synth.mixed_batch(env["specs"])
     t = _dev(env, mb)
-    opts = psr.Options(precision=psr.PSR_MIXED)
+    opts = psr.Options(precision=psr.PSR_MIXED, persistent=persistent)
     out = _multi(env, t, opts)
     Y, T, st = out["Y"].cpu().numpy(), out["T"].cpu().numpy(), out["status"].cpu().numpy()
     fn = out["fnorm"].cpu().numpy()
@@ -68,7 +71,8 @@ def test_uneven_batch_full_size(env):
         bc = mb["batches"][c]
         d = {k: torch.tensor(np.ascontiguousarray(getattr(bc, k)), dtype=torch.float64, device=env["dev"])
              for k in ("Y_in", "T_in", "tau", "P", "Y0", "T0")}
-        ref = psr.batch_solve(gm, d["Y_in"], d["T_in"], d["tau"], d["P"], d["Y0"], d["T0"], opts=opts)
+        ref = psr.batch_solve(gm, d["Y_in"], d["T_in"], d["tau"], d["P"], d["Y0"], d["T0"],
+                              opts=psr.Options(precision=psr.PSR_MIXED))
         Yr, Tr, sr = ref["Y"].cpu().numpy(), ref["T"].cpu().numpy(), ref["status"].cpu().numpy()
         Yc = _rows(mb, Y, c, spec.K)
         # the block-per-reactor path accumulates its Jacobian with atomics from several
@@ -76,7 +80,7 @@ def test_uneven_batch_full_size(env):
         # marginal reactor may converge in the other precision's launch (status 0 vs 5)
         cm, cr = np.isin(st[mem], psr.CONVERGED_STATES), np.isin(sr, psr.CONVERGED_STATES)
         assert np.mean(cm == cr) >= 0.99, f"class {c}: convergence differs"
-        if spec.K + 1 <= 64:
+        if spec.K + 1 <= 64 and not persistent:
             assert np.array_equal(st[mem], sr), f"class {c}: statuses differ"
         both = np.isin(st[mem], psr.CONVERGED_STATES) & np.isin(sr, psr.CONVERGED_STATES) & \
             (np.abs(T[mem] - Tr) < 1.0)
@@ -102,6 +106,84 @@ def test_uneven_batch_full_size(env):
             assert abs(T[mem[j]] - r.x[-1]) <= T_ABS
 
 
+def _agree(st_a, st_b, Ta, Tb, min_frac=0.99):
+    """Two solves of the same reactors: convergence agrees on >= min_frac of them, and rows
+    both converged on the same branch match within the parity bar."""
+    ca, cb = np.isin(st_a, psr.CONVERGED_STATES), np.isin(st_b, psr.CONVERGED_STATES)
+    assert np.mean(ca == cb) >= min_frac
+    both = ca & cb & (np.abs(Ta - Tb) < 1.0)
+    assert both.mean() >= min_frac - 0.01
+    return both
+
+
+@pytest.mark.parametrize("precision", [psr.PSR_MIXED, psr.PSR_FP64])
+def test_persistent_launch_matches_per_class_launches(env, precision):
+    """The one persistent launch (block-solver classes first, then warp-solver classes, the
+    FP64 re-solve in the same kernel) against one launch sequence per mechanism on forked
+    streams, on 4096 reactors of the uneven batch: the same convergence and, row by row, the
+    same roots within the parity bar. (Not bit for bit: the same solver code compiled into
+    another kernel may contract and order its floating-point operations differently.)"""
+    mb = synth.mixed_batch(env["specs"], B=4096)
+    t = _dev(env, mb)
+    a = _multi(env, t, psr.Options(precision=precision, persistent=1, handoff=0))
+    b = _multi(env, t, psr.Options(precision=precision, persistent=0, handoff=0))
+    sa, sb = a["status"].cpu().numpy(), b["status"].cpu().numpy()
+    Ya, Yb, Ta, Tb = (x.cpu().numpy() for x in (a["Y"], b["Y"], a["T"], b["T"]))
+    assert np.isin(sa, psr.CONVERGED_STATES).mean() >= 0.95
+    _agree(sa, sb, Ta, Tb)
+    for c, spec in enumerate(env["specs"]):
+        mem = mb["members"][c]
+        Yc_a, Yc_b = _rows(mb, Ya, c, spec.K), _rows(mb, Yb, c, spec.K)
+        both = _agree(sa[mem], sb[mem], Ta[mem], Tb[mem], 0.98)
+        big = Yc_b[both] > Y_MIN
+        rel = np.where(big, np.abs(Yc_a[both] - Yc_b[both]) / np.where(big, Yc_b[both], 1.0), 0.0).max(axis=1)
+        off = (rel > Y_REL) | (np.abs(Ta[mem][both] - Tb[mem][both]) > T_ABS)
+        assert off.mean() <= (0.0 if spec.K + 1 <= 64 else 0.01), f"class {c}: {off.sum()} rows off the bar"
+
+
+def test_persistent_launch_on_the_block_path(env):
+    """PSR_PATH_BLOCK puts every class on the block solver inside the persistent launch
+    (phase 2 empty): converged rows at ||F|| <= 1e-8 that conserve elements and match the
+    default launch's roots."""
+    mb = synth.mixed_batch(env["specs"], B=2048)
+    t = _dev(env, mb)
+    a = _multi(env, t, psr.Options(precision=psr.PSR_MIXED, path=psr.PSR_PATH_BLOCK, persistent=1))
+    b = _multi(env, t, psr.Options(precision=psr.PSR_MIXED))
+    sa, sb = a["status"].cpu().numpy(), b["status"].cpu().numpy()
+    Ta, Tb = a["T"].cpu().numpy(), b["T"].cpu().numpy()
+    conv = np.isin(sa, psr.CONVERGED_STATES)
+    assert conv.mean() >= 0.95
+    assert np.all(a["fnorm"].cpu().numpy()[conv] <= 1e-8)
+    both = _agree(sa, sb, Ta, Tb, 0.98)
+    assert np.abs(Ta[both] - Tb[both]).max() <= T_ABS
+    Ya = a["Y"].cpu().numpy()
+    for c, (spec, mech) in enumerate(zip(env["specs"], env["mechs"])):
+        mem = mb["members"][c]
+        bc = mb["batches"][c]
+        Yc = _rows(mb, Ya, c, spec.K)
+        ok = conv[mem]
+        elem = ((Yc[ok] - bc.Y_in[ok]) / mech.W) @ mech.comp
+        assert np.max(np.abs(elem)) <= 1e-12
+
+
+def test_spin_limit_bounds_the_wait(env):
+    """With spin_limit = 1 a block of the persistent launch that finds no re-solve entry
+    published yet gives up at once instead of waiting: the call still completes, every
+    status is a valid code, and what converged meets the tolerance."""
+    mb = synth.mixed_batch(env["specs"], B=1024)
+    t = _dev(env, mb)
+    out = _multi(env, t, psr.Options(precision=psr.PSR_MIXED, persistent=1, spin_limit=1, mixed_max_newton=20))
+    st = out["status"].cpu().numpy()
+    assert np.all(np.isin(st, [psr.PSR_CONVERGED, psr.PSR_REFINE_FALLBACK, psr.PSR_MAX_ITER,
+                               psr.PSR_NONFINITE, psr.PSR_TS_EXHAUSTED]))
+    conv = np.isin(st, psr.CONVERGED_STATES)
+    assert np.all(out["fnorm"].cpu().numpy()[conv] <= 1e-8)
+    with pytest.raises(psr.PsrError):
+        _multi(env, t, psr.Options(spin_limit=-1))
+    with pytest.raises(psr.PsrError):
+        _multi(env, t, psr.Options(persistent=2))
+
+
 def test_bad_mechanism_id_is_reported(env):
     mb = synth.mixed_batch(env["specs"], B=96)
     t = _dev(env, mb)
@@ -117,15 +199,17 @@ def test_bad_mechanism_id_is_reported(env):
         psr.batch_solve_multi([], t["mech_id"], t["row_off"], t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"])
 
 
-def test_graph_capture_replays_the_call(env):
-    """The call captured into a CUDA graph (bucketing, three solver launches on forked
-    streams, the FP64 re-solves) and replayed gives the eager call's results."""
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_graph_capture_replays_the_call(env, persistent):
+    """The call captured into a CUDA graph (bucketing, then three solver launches on forked
+    streams and the FP64 re-solves, or the one persistent launch) and replayed gives the
+    eager call's results."""
     import torch
     mb = synth.mixed_batch(env["specs"], B=384)
     t = _dev(env, mb)
     # without the handoff of stragglers, which depends on timing, so that warp-path rows
     # are bit-reproducible
-    opts = psr.Options(precision=psr.PSR_MIXED, handoff=0)
+    opts = psr.Options(precision=psr.PSR_MIXED, handoff=0, persistent=persistent)
     eager = _multi(env, t, opts)
     torch.cuda.synchronize()
     out = {k: torch.empty_like(v) for k, v in eager.items()}

@@ -378,15 +378,17 @@ def test_autotune_picks_a_shape_with_identical_results(dev):
         psr.autotune(gm, t["Y_in"][:0], t["T_in"][:0], t["tau"][:0], t["P"][:0], t["Y0"][:0], t["T0"][:0])
 
 
+@pytest.mark.parametrize("block_threads", [512, 256])
 @pytest.mark.parametrize("precision", [psr.PSR_FP64, psr.PSR_MIXED])
-def test_block_path_on_the_k53_batch(dev, precision):
-    """The same 4096-reactor K = 53 batch with one 512-thread block per reactor (the
-    path larger mechanisms take) instead of one warp: every converged reactor has
+def test_block_path_on_the_k53_batch(dev, precision, block_threads):
+    """The same 4096-reactor K = 53 batch with one block of 512 or 256 threads per reactor
+    (the path larger mechanisms take) instead of one warp: every converged reactor has
     ||F|| <= 1e-8 and conserves elements, 32 sampled reactors match the oracle."""
     _, mech, batch = workload("k53_b4096")
     t = to_dev(batch, dev)
     out = psr.batch_solve(gpu_mech("k53_b4096"), t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"],
-                          opts=psr.Options(precision=precision, path=psr.PSR_PATH_BLOCK))
+                          opts=psr.Options(precision=precision, path=psr.PSR_PATH_BLOCK,
+                                           block_threads=block_threads))
     Y, T, st = out["Y"].cpu().numpy(), out["T"].cpu().numpy(), out["status"].cpu().numpy()
     conv = np.isin(st, psr.CONVERGED_STATES)
     assert conv.mean() >= 0.99
@@ -395,7 +397,7 @@ def test_block_path_on_the_k53_batch(dev, precision):
     assert np.max(np.abs(elem)) <= 1e-12
     idx = [int(i) for i in np.random.Generator(np.random.PCG64(5)).choice(batch.B, 32, replace=False)]
     ref = oracle_solution_pool("k53_b4096", idx)          # the sample of the warp-path test (cached)
-    n_ok, _ = compare_roots("k53_b4096", idx, ref, Y[idx], T[idx], st[idx], f"k53 block path prec={precision}")
+    n_ok, _ = compare_roots("k53_b4096", idx, ref, Y[idx], T[idx], st[idx], f"k53 block path prec={precision} bt={block_threads}")
     assert n_ok >= 28
 
 

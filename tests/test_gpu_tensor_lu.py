@@ -70,10 +70,11 @@ def test_tensor_core_lu_small_n_uses_cuda_cores(dev):
                               torch.zeros((1, 128), dtype=torch.float64, device=dev), 2)
 
 
+@pytest.mark.parametrize("block_threads", [512, 256])
 @pytest.mark.parametrize("mode", [psr.PSR_LU_TF32, psr.PSR_LU_3XTF32])
-def test_k200_solves_with_tensor_core_lu(dev, mode):
+def test_k200_solves_with_tensor_core_lu(dev, mode, block_threads):
     """304 reactors of the K = 200 batch (two per SM) in the mixed form with the
-    tensor-core trailing update: converged reactors at ||F|| <= 1e-8 with elements
+    tensor-core trailing update, on blocks of 512 or 256 threads: converged reactors at ||F|| <= 1e-8 with elements
     conserved, and on the FP64 form's branch the FP64 form's roots within the bar."""
     import torch
     spec, mech, batch = workload("k200_b2048")
@@ -84,7 +85,7 @@ def test_k200_solves_with_tensor_core_lu(dev, mode):
     ref = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"],
                           opts=psr.Options(precision=psr.PSR_FP64))
     got = psr.batch_solve(gm, t["Y_in"], t["T_in"], t["tau"], t["P"], t["Y0"], t["T0"],
-                          opts=psr.Options(precision=psr.PSR_MIXED, lu_tensor=mode))
+                          opts=psr.Options(precision=psr.PSR_MIXED, lu_tensor=mode, block_threads=block_threads))
     rs, gs = ref["status"].cpu().numpy(), got["status"].cpu().numpy()
     rc, gc = np.isin(rs, psr.CONVERGED_STATES), np.isin(gs, psr.CONVERGED_STATES)
     assert gc.mean() >= 0.97
