@@ -774,6 +774,8 @@ def run_ours(args):
         "clocks": clocks,
         "peaks": {**peaks, "clocks": peak_clocks},
     }
+    if "persistent_launch" in head:
+        line["persistent_launch"] = head["persistent_launch"]
     if extra:
         line["workloads"] = extra
     if not args.no_cpu_baseline and not args.batch:
