@@ -127,7 +127,7 @@ typedef struct {
     int32_t path;           /* PSR_PATH_AUTO (default): one warp per reactor when K + 1 <= 64,
                                else one thread block (block_threads); PSR_PATH_WARP / PSR_PATH_BLOCK force
                                one (PSR_E_UNSUPPORTED where the mechanism does not fit it) */
-    int32_t handoff;        /* -1 (default: 75 for PSR_FP64, 0 for PSR_MIXED) or 0..100. One warp
+    int32_t handoff;        /* -1 (default: 75 for PSR_FP64, 90 for PSR_MIXED) or 0..100. One warp
                                per reactor only: once this percentage of the launch's working
                                warps found its work queue empty, the reactors still running stop
                                at their next Newton iteration and a second launch continues them

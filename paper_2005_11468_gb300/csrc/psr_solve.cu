@@ -309,9 +309,10 @@ Opts to_opts(const psr_options *po) {
     o.jac_age = s.jac_age < 1 ? 1 : s.jac_age;
     o.ts_linear = s.ts_linear;
     o.energy = s.energy;
-    // handoff by default where it was measured to pay: the FP64 form (at K = 53 the block
-    // solver finishes a straggler ~1.6x sooner than a warp with the FP64 LU, ~1.3x with FP32)
-    o.handoff_pct = s.handoff >= 0 ? s.handoff : (s.precision == PSR_FP64 ? 75 : 0);
+    // handoff thresholds measured at K = 53 with the 256-thread block solver continuing (it
+    // finishes a straggler ~1.6x sooner than a warp with the FP64 LU, ~1.3x with FP32): the
+    // FP64 form at 75 %, the mixed form only at the very end of the launch, 90 %
+    o.handoff_pct = s.handoff >= 0 ? s.handoff : (s.precision == PSR_FP64 ? 75 : 90);
     o.lu_tc = s.lu_tensor;
     o.mixed_fb = s.mixed_fallback;
     o.block_threads = s.block_threads;
