@@ -521,6 +521,7 @@ def solve_summary(ctx, r, peaks, traffic=None):
     roof = roofline(work_counts(r["spec"], m["nfev"], m["iters"], "mixed"), s_m, peaks, traffic)
     roof64 = roofline(work_counts(r["spec"], f["nfev"], f["iters"], "fp64"), s_f, peaks)
     return {"value": value, "unit": UNIT, "ms_per_step": 1e3 * s_m, "steps": k,
+            "ms_steps": [round(x, 3) for x in m["ms"]],
             "converged_fraction": m["conv"] / B, "refine_fallback": m["fallback"],
             "newton_iters_mean": float(np.mean(m["iters"])), "newton_iters_median": float(np.median(m["iters"])),
             "residual_evals_mean": float(np.mean(m["nfev"])),
@@ -767,6 +768,7 @@ def run_ours(args):
         "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64 residual / f32 Jacobian+LU", "data": "synthetic",
         "config": workload_config(args.workload, ctx.world, B),
+        **{k: head[k] for k in ("ms_steps",) if k in head},
         **{k: head[k] for k in ("fp64_form", "mixed_vs_fp64", "converged_fraction", "newton_iters_mean",
                                 "newton_iters_median", "residual_evals_mean", "roofline")},
         "e2e": head["e2e"],
@@ -783,8 +785,9 @@ def run_ours(args):
             line["cpu_baseline"] = cpu_baseline_mixed((host_cores(), host_cores(), max(1, host_cores() // 4)))
         else:
             spec = synth.workload_mechanism(args.workload)
-            n_all = 256 if spec.K <= 60 and spec.soot is None else 2 * host_cores()
-            line["cpu_baseline"] = cpu_baseline(args.workload, n_all, 8 if spec.soot is None else 2)
+            B_w = synth.WORKLOADS[args.workload]["B"]
+            n_all = min(B_w, 256 if spec.K <= 60 and spec.soot is None else 2 * host_cores())
+            line["cpu_baseline"] = cpu_baseline(args.workload, n_all, min(B_w, 8 if spec.soot is None else 2))
     print(json.dumps(line))
     ctx.close()
 
