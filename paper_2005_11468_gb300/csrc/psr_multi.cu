@@ -8,13 +8,16 @@
 //   1. block-solver classes (K + 1 > 64, or every class when the block path is forced), in
 //      order of decreasing K: the whole block takes one reactor at a time from a single
 //      atomic counter over the concatenated class lists, so the longest solves start first;
+//      in the mixed form an FP64 re-solve already listed (below) is taken before the next
+//      first-pass reactor;
 //   2. warp-solver classes, again largest K first: each warp with a shared-memory slice
 //      takes reactors from a second counter;
 //   3. mixed form only: the FP64 re-solve of reactors the FP32-Jacobian passes left
-//      unconverged (continued from the FP32 iterate, then restarted from the initial guess
-//      where that fails), one block per reactor. Phases 1-2 append such reactors to a list
-//      as they finish, so a block that ran out of first-pass work re-solves them while other
-//      blocks are still busy, instead of a second launch after the slowest first-pass reactor.
+//      unconverged (warp-solver classes continued from the FP32 iterate, then restarted from
+//      the initial guess where that fails; block-solver classes restarted), one block per
+//      reactor. Phases 1-2 append such reactors to a list as they finish, so blocks re-solve
+//      them while others are still busy, instead of a second launch after the slowest
+//      first-pass reactor.
 //
 // The wait in phase 3 (for a list entry, or for the end of the first pass) is bounded by
 // Opts-independent spin_limit polls; a block that gives up sets the error word and leaves
@@ -111,6 +114,54 @@ __device__ unsigned long long claim_resolve(const MultiArgs &a, int total) {
     return ~0ull;
 }
 
+// Claim without waiting (thread 0): a re-solve entry some producer has already reserved
+// (it publishes it right after), or ~0 when none is reserved beyond the claims so far.
+__device__ unsigned long long try_claim_resolve(const MultiArgs &a) {
+    volatile int *qf = a.ctl + kQF, *nf = a.ctl + kNF;
+    while (true) {
+        const int cur = *qf;
+        if (cur >= *nf) return ~0ull;
+        if (atomicCAS(a.ctl + kQF, cur, cur + 1) != cur) continue;   // another block took it
+        volatile unsigned long long *slot = a.relist + cur;
+        for (long long it = 0; it < a.spin_limit; ++it) {
+            const unsigned long long v = *slot;
+            if (v != ~0ull) return v;
+            __nanosleep(100);
+        }
+        atomicExch(a.ctl + kErr, 1);
+        return ~0ull;
+    }
+}
+
+// FP64 re-solve (mixed form) of re-solve entry v, one block: warp-solver classes are first
+// continued from the FP32 pass's final iterate, then restarted from the initial guess where
+// that fails; block-solver classes are restarted at once (as the per-mechanism launches do:
+// at K = 200 the FP32 pass's failures end in exhausted pseudo-time stepping, whose iterate
+// the FP64 continuation almost never converges).
+__device__ void resolve_fp64(const MultiArgs &a, const Batch &bt, blk::BCtx &cx, char *smem,
+                             unsigned long long v) {
+    const int c = int(v >> 32);
+    const int64_t r = int64_t(v & 0xffffffffull);
+    const DevMech &M = a.cls[c].M;
+    cx.M = M;
+    cx.K = M.K;
+    cx.n = M.K + 1;
+    double *Jg = a.cls[c].j_smem64 ? nullptr : reinterpret_cast<double *>(a.jglob + blockIdx.x * a.jslot);
+    const blk::BWS<double> w = blk::bcarve<double>(smem, M.K, M.I, M.n_troe, M.K + 1, Jg, 0);
+    Batch b2 = bt;
+    b2.fallback = 1;   // counters add up; success reports PSR_REFINE_FALLBACK
+    if (a.fb_passes == 2 && c >= a.n_block) {
+        // continued from the FP32 pass's final iterate (read before it is overwritten)
+        Batch bc = b2;
+        bc.Y0 = bt.Y_out;
+        if (cx.o.energy != PSR_FIXED_T) bc.T0 = bt.T_out;   // else T0 is the specified temperature
+        blk::b_solve_one<double>(cx, w, bc, r);
+        const int32_t s = bt.status[r];   // written by thread 0 before the solver's last barrier
+        if (s == PSR_CONVERGED || s == PSR_REFINE_FALLBACK) return;
+    }
+    blk::b_solve_one<double>(cx, w, b2, r);   // restarted from the initial guess
+}
+
 template <class TJ>
 __global__ void __launch_bounds__(kMT, kMinB) multi_solve_kernel(MultiArgs a, Batch bt, Opts o1, Opts o) {
     extern __shared__ __align__(128) char smem[];
@@ -124,18 +175,36 @@ __global__ void __launch_bounds__(kMT, kMinB) multi_solve_kernel(MultiArgs a, Ba
         total += s_cnt[c];
         if (c < a.n_block) nB += s_cnt[c];
     }
-    // ---- phase 1: block-solver classes, one block per reactor
+    blk::BCtx cx64;   // the FP64 re-solves (mixed form)
+    cx64.o = o;
+    cx64.mult = bt.rate_mult;
+    cx64.fn = INFINITY;
+    constexpr unsigned long long kFirst = 1ull << 63;   // tags a first-pass claim
+    // ---- phase 1: block-solver classes, one block per reactor; in the mixed form an FP64
+    // re-solve already listed goes first (the longest work starts earliest)
     if (nB > 0) {
         blk::BCtx cx;
         cx.o = o1;
         cx.mult = bt.rate_mult;
         cx.fn = INFINITY;
         while (true) {
-            if (t == 0) s_claim = static_cast<unsigned long long>(atomicAdd(a.ctl + kQB, 1));
+            if (t == 0) {
+                unsigned long long v = ~0ull;
+                if (sizeof(TJ) == 4 && a.fb_passes > 0) v = try_claim_resolve(a);
+                if (v == ~0ull) v = kFirst | static_cast<unsigned long long>(atomicAdd(a.ctl + kQB, 1));
+                s_claim = v;
+            }
             __syncthreads();
+            const unsigned long long v = s_claim;
+            __syncthreads();
+            if constexpr (sizeof(TJ) == 4) {
+                if (!(v & kFirst)) {
+                    resolve_fp64(a, bt, cx64, smem, v);
+                    continue;
+                }
+            }
             int64_t r = 0;
-            const int c = locate(a, s_cnt, 0, a.n_block, int(s_claim), r);
-            __syncthreads();
+            const int c = locate(a, s_cnt, 0, a.n_block, int(v & 0x7fffffffull), r);
             if (c < 0) break;
             const DevMech &M = a.cls[c].M;
             cx.M = M;
@@ -176,36 +245,13 @@ __global__ void __launch_bounds__(kMT, kMinB) multi_solve_kernel(MultiArgs a, Ba
     // ---- phase 3 (mixed form): FP64 re-solve of the reactors the first pass left
     if constexpr (sizeof(TJ) == 4) {
         if (a.fb_passes <= 0) return;
-        blk::BCtx cx;
-        cx.o = o;
-        cx.mult = bt.rate_mult;
-        cx.fn = INFINITY;
         while (true) {
             if (t == 0) s_claim = claim_resolve(a, total);
             __syncthreads();
             const unsigned long long v = s_claim;
             __syncthreads();
             if (v == ~0ull) break;
-            const int c = int(v >> 32);
-            const int64_t r = int64_t(v & 0xffffffffull);
-            const DevMech &M = a.cls[c].M;
-            cx.M = M;
-            cx.K = M.K;
-            cx.n = M.K + 1;
-            double *Jg = a.cls[c].j_smem64 ? nullptr : reinterpret_cast<double *>(a.jglob + blockIdx.x * a.jslot);
-            const blk::BWS<double> w = blk::bcarve<double>(smem, M.K, M.I, M.n_troe, M.K + 1, Jg, 0);
-            Batch b2 = bt;
-            b2.fallback = 1;   // counters add up; success reports PSR_REFINE_FALLBACK
-            if (a.fb_passes == 2) {
-                // continued from the FP32 pass's final iterate (read before it is overwritten)
-                Batch bc = b2;
-                bc.Y0 = bt.Y_out;
-                if (o.energy != PSR_FIXED_T) bc.T0 = bt.T_out;   // else T0 is the specified temperature
-                blk::b_solve_one<double>(cx, w, bc, r);
-                const int32_t s = bt.status[r];   // written by thread 0 before the solver's last barrier
-                if (s == PSR_CONVERGED || s == PSR_REFINE_FALLBACK) continue;
-            }
-            blk::b_solve_one<double>(cx, w, b2, r);   // restarted from the initial guess
+            resolve_fp64(a, bt, cx64, smem, v);
         }
     }
 }
