@@ -649,7 +649,8 @@ def measure_multi(ctx, steps, warmup, steps64, peaks, sampler=None, e2e=False):
                                  "how": "persistent = 1: the bucketing kernel and one multi_solve_kernel over "
                                         "all mechanisms, FP64 re-solves inside (direct call)"},
            # per step: the bucketing kernel, then per mechanism the solver launch and the FP64
-           # re-solve passes (warp path: two list/re-solve pairs; block path: one)
+           # re-solve passes (warp path: the handoff list and continuation, then two
+           # list/re-solve pairs; block path: one pair)
            "gpu_launches_per_step": 1 + sum(7 if sp.K + 1 <= 64 else 3 for sp in specs)}
     if e2e:
         res["e2e"] = {"value": e_conv / e_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
