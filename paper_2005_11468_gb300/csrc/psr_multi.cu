@@ -4,7 +4,7 @@
 //
 // The method is the hybrid damped Newton / pseudo-transient scheme of Sec. 3 on the
 // residual of Eqs. (2)-(3), as in the one-mechanism solvers; this file only schedules it.
-// A block of kBT threads runs three phases:
+// A block of kMT = 256 threads runs three phases:
 //   1. block-solver classes (K + 1 > 64, or every class when the block path is forced), in
 //      order of decreasing K: the whole block takes one reactor at a time from a single
 //      atomic counter over the concatenated class lists, so the longest solves start first;
@@ -20,10 +20,10 @@
 //      first-pass reactor.
 //
 // The wait in phase 3 (for a list entry, or for the end of the first pass) is bounded by
-// Opts-independent spin_limit polls; a block that gives up sets the error word and leaves
-// its entry unsolved (its status stays the FP32 pass's failure). Every producer it waits
-// for is a reactor already being solved by a resident warp or block, so the wait ends when
-// that reactor does.
+// psr_options.spin_limit polls about 1 us apart; a block that gives up sets the error word
+// and leaves its entry unsolved (its status stays the FP32 pass's failure). Every producer
+// it waits for is a reactor already being solved by a resident warp or block, so the wait
+// ends when that reactor does.
 //
 // Built once per first-pass Jacobian precision: PSR_MULTI_TJ (float | double) and the name
 // of the host entry, PSR_MULTI_ENTRY, come from the build.
