@@ -93,7 +93,7 @@ typedef struct {
     double step_atol_t;     /* 1e-10 K */
     double ts_rtol;         /* 1e-4: a pseudo-time step is solved when |dx_j| <= ts_rtol |x_j| + ts_atol_j */
     double ts_atol_y;       /* 1e-10 (temperature uses ts_rtol) */
-    double dt0_over_tau;    /* 1e-10: first pseudo-time step / tau */
+    double dt0_over_tau;    /* 1e-6: first pseudo-time step / tau */
     double dt_shrink;       /* 0.25: dt factor after a failed pseudo-time step */
     double y_floor;         /* 1e-10: iterates keep Y_k >= -y_floor */
     double t_min, t_max;    /* 200 K, 5000 K: temperature bounds of the iterates */

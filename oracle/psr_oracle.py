@@ -342,7 +342,7 @@ class Options:
                                 #   ones (all when 0) are solved by damped Newton to ts_rtol
     ts_rtol: float = 1e-4       # a time step is solved when its undamped step is below
     ts_atol_y: float = 1e-10    #   ts_rtol |x_j| + ts_atol_j
-    dt0_over_tau: float = 1e-10
+    dt0_over_tau: float = 1e-6    # first pseudo-time step / tau
     dt_shrink: float = 0.25     # dt factor after a failed pseudo-time step
     y_floor: float = 1e-10      # iterates keep Y_k >= -y_floor
     t_min: float = 200.0

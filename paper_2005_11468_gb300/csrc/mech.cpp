@@ -528,7 +528,7 @@ void psr_options_default(psr_options *o) {
     o->step_atol_t = 1e-10;
     o->ts_rtol = 1e-4;
     o->ts_atol_y = 1e-10;
-    o->dt0_over_tau = 1e-10;
+    o->dt0_over_tau = 1e-6;
     o->dt_shrink = 0.25;
     o->y_floor = 1e-10;
     o->t_min = 200.0;

@@ -112,7 +112,7 @@ class Options:
     step_atol_t: float = 1e-10
     ts_rtol: float = 1e-4
     ts_atol_y: float = 1e-10
-    dt0_over_tau: float = 1e-10
+    dt0_over_tau: float = 1e-6
     dt_shrink: float = 0.25
     y_floor: float = 1e-10
     t_min: float = 200.0
