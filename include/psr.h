@@ -107,9 +107,10 @@ typedef struct {
     int32_t warps_per_block;/* 0 = default (2); at most 4 */
     int32_t blocks_per_sm;  /* 0 = as many as fit */
     int32_t mixed_fallback; /* PSR_MIXED: what the FP32-Jacobian launch leaves unconverged is
-                               solved again with the FP64 Jacobian: 2 (default) first continued
-                               from that launch's final iterate, then restarted from the initial
-                               guess where the continuation fails; 1 restart only; 0 none */
+                               solved again with the FP64 Jacobian: 2 (default) the reactors it
+                               stopped at its iteration cap first continued from its final
+                               iterate, then everything left restarted from the initial guess;
+                               1 restart only; 0 none */
     int32_t jacobian;       /* PSR_JAC_ANALYTIC (default) or PSR_JAC_FD: central differences
                                as the paper builds it (Sec. 1), K + 1 <= 64 gas mechanisms */
     int32_t mixed_max_newton; /* -1 (default: 300 for gas mechanisms, 200 with soot moments):

@@ -133,11 +133,11 @@ __device__ unsigned long long try_claim_resolve(const MultiArgs &a) {
     }
 }
 
-// FP64 re-solve (mixed form) of re-solve entry v, one block: warp-solver classes are first
-// continued from the FP32 pass's final iterate, then restarted from the initial guess where
-// that fails; block-solver classes are restarted at once (as the per-mechanism launches do:
-// at K = 200 the FP32 pass's failures end in exhausted pseudo-time stepping, whose iterate
-// the FP64 continuation almost never converges).
+// FP64 re-solve (mixed form) of re-solve entry v, one block: warp-solver reactors that the
+// FP32 pass stopped at its iteration cap are first continued from its final iterate, then
+// restarted from the initial guess where that fails; the others (block-solver classes, and
+// reactors whose FP32 pass ended in exhausted pseudo-time stepping, an iterate the FP64
+// continuation almost never finishes) are restarted at once, as the per-mechanism launches do.
 __device__ void resolve_fp64(const MultiArgs &a, const Batch &bt, blk::BCtx &cx, char *smem,
                              unsigned long long v) {
     const int c = int(v >> 32);
@@ -150,7 +150,7 @@ __device__ void resolve_fp64(const MultiArgs &a, const Batch &bt, blk::BCtx &cx,
     const blk::BWS<double> w = blk::bcarve<double>(smem, M.K, M.I, M.n_troe, M.K + 1, Jg, 0);
     Batch b2 = bt;
     b2.fallback = 1;   // counters add up; success reports PSR_REFINE_FALLBACK
-    if (a.fb_passes == 2 && c >= a.n_block) {
+    if (a.fb_passes == 2 && c >= a.n_block && bt.status[r] == PSR_MAX_ITER) {
         // continued from the FP32 pass's final iterate (read before it is overwritten)
         Batch bc = b2;
         bc.Y0 = bt.Y_out;

@@ -31,6 +31,7 @@ __global__ void collect_unconverged(int64_t B, const int32_t *in_list, const int
         const int64_t r = in_list ? int64_t(in_list[p]) : p;
         const int32_t s = status[r];
         const bool take = mode == 1 ? s == kStatusHandoff
+                          : mode == 3 ? s == PSR_MAX_ITER
                                     : (s != PSR_CONVERGED && (mode == 0 || s != PSR_REFINE_FALLBACK));
         if (take) list[atomicAdd(len, 1)] = int32_t(r);
     }
@@ -503,15 +504,17 @@ int launch_mixed(const Mech &m, const Batch &bt, const Opts &o, int wpb_req, int
             rc = block_resolve_list(m, bc, o1, PSR_MIXED, st, q1);
         }
     }
-    // FP64 re-solve of what the FP32 launch left unconverged: with mixed_fallback = 2 first
-    // continued from the FP32 launch's final iterate, then restarted from the initial guess
-    // for whatever the continuation leaves; with 1, only the restart
+    // FP64 re-solve of what the FP32 launch left unconverged: with mixed_fallback = 2 the
+    // reactors it stopped at its iteration cap are first continued from its final iterate
+    // (most converge in a few dozen iterations), then whatever is left, including the ones
+    // that ended in exhausted pseudo-time stepping (whose iterate an FP64 continuation almost
+    // never finishes), is restarted from the initial guess; with 1, only the restart
     const int passes = o.mixed_fb == 2 ? 2 : 1;
     for (int pass = 0; pass < passes && rc == PSR_OK; ++pass) {
         const bool from_iterate = passes == 2 && pass == 0;
         cudaMemsetAsync(len, 0, sizeof(int32_t), st);
         collect_unconverged<<<unsigned((B + 255) / 256), 256, 0, st>>>(bt.B, bt.list, bt.list_len, b1.status, list,
-                                                                       len, pass == 0 ? 0 : 2);
+                                                                       len, pass == 0 ? (passes == 2 ? 3 : 0) : 2);
         e = cudaGetLastError();
         if (e != cudaSuccess) {
             rc = cuda_error("collect_unconverged launch", e);
