@@ -265,7 +265,22 @@ int block_solve(const Mech &m, const Batch &bt, const Opts &o, int precision, bo
             b2.list = list;
             b2.list_len = len;
             b2.fallback = 1;
+#if PSR_BLOCK_THREADS == 256
+            // The list is a small part of the batch. When the whole batch holds at most 16
+            // reactors per SM the list is likely shorter than one 512-thread block per SM, and
+            // 512 threads per reactor finish each reactor sooner (K = 200, 2048 reactors: 1.23
+            // -> 1.16 s per mixed step); larger batches and class lists keep two 256-thread
+            // blocks per SM (the uneven batch's K = 200 class: 2.48 s, 2.56 s with 512 threads).
+            int dev = 0, nsm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            if (!bt.list && B <= size_t(16) * size_t(nsm))
+                rc = bt512::block_resolve_list(m, b2, o, PSR_FP64, st, scr + 1);
+            else
+                rc = launch_block<double>(m, b2, o, bps_req, st, scr + 1);
+#else
             rc = launch_block<double>(m, b2, o, bps_req, st, scr + 1);
+#endif
         }
     }
     cudaFreeAsync(scr, st);
